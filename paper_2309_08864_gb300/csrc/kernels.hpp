@@ -1,0 +1,34 @@
+// kernels.hpp -- host-side entry points of the device kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "../../include/so2dr.h"
+#include "stencil.cuh"
+
+namespace so2dr {
+
+// Tiling and shared-memory size of a stencil launch for the plan's geometry.
+struct LaunchShape {
+    dim3 grid, block;
+    size_t smem;
+    int lx, ly, tx, ty;
+    bool ok;
+};
+
+LaunchShape stencil_launch_shape(int shape, int r, int depth, int64_t ny, int64_t nx, int csize);
+
+// Largest fused depth the stencil kernel supports for this geometry.
+int stencil_max_depth(int shape, int r, int csize);
+
+// Launches the temporal-blocking kernel.  Returns cudaSuccess or the error.
+cudaError_t launch_stencil(int dtype, int shape, int r, const StencilArgs& a, const LaunchShape& ls,
+                           cudaStream_t s);
+
+// Per-dtype instantiations (one translation unit each).
+cudaError_t launch_stencil_f64(int shape, int r, const StencilArgs& a, const LaunchShape& ls, cudaStream_t s);
+cudaError_t launch_stencil_f32(int shape, int r, const StencilArgs& a, const LaunchShape& ls, cudaStream_t s);
+cudaError_t launch_stencil_bf16(int shape, int r, const StencilArgs& a, const LaunchShape& ls, cudaStream_t s);
+cudaError_t launch_stencil_f16(int shape, int r, const StencilArgs& a, const LaunchShape& ls, cudaStream_t s);
+
+}  // namespace so2dr

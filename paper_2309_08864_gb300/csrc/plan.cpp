@@ -1,0 +1,602 @@
+// plan.cpp -- chunking, rounds, arena layout and op lists (host only).
+#include "plan.hpp"
+
+#include <algorithm>
+#include <cmath>
+#include <limits>
+
+namespace so2dr {
+
+namespace {
+constexpr int64_t kAlign = 256;
+int64_t align_up(int64_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+int64_t floor_mod(int64_t a, int64_t m) { return ((a % m) + m) % m; }
+}  // namespace
+
+int64_t elem_size(int dtype) {
+    switch (dtype) {
+        case SO2DR_F64: return 8;
+        case SO2DR_F32: return 4;
+        case SO2DR_BF16: return 2;
+        case SO2DR_F16: return 2;
+        default: return 0;
+    }
+}
+
+int num_coeffs(int ndim, int radius, int kind) {
+    if (kind == SO2DR_STAR) return 1 + 2 * radius * ndim;
+    if (kind == SO2DR_BOX) {
+        int w = 2 * radius + 1, n = 1;
+        for (int a = 0; a < ndim; ++a) n *= w;
+        return n;
+    }
+    if (kind == SO2DR_VARCOEF_STAR) return 0;
+    return -1;
+}
+
+std::vector<int> launch_depths(int k, int k_on) {
+    std::vector<int> v;
+    for (int j = 0; j < k / k_on; ++j) v.push_back(k_on);
+    if (k % k_on) v.push_back(k % k_on);
+    return v;
+}
+
+int round_steps(int64_t T, int k_off, int t) {
+    int64_t rounds = (T + k_off - 1) / k_off;
+    if (t == rounds - 1 && T % k_off != 0) return (int)(T % k_off);
+    return k_off;
+}
+
+double Plan::cell_updates() const {
+    int64_t inner = 1;
+    int64_t ext[3] = {n0, ny, nx};
+    for (int a = 0; a < 3; ++a) {
+        bool used = (a == 0) || (a == 1 && ndim == 3) || (a == 2);
+        if (!used) continue;
+        int64_t m = ext[a] - 2 * r;
+        inner *= std::max<int64_t>(0, m);
+    }
+    return (double)inner * (double)T;
+}
+
+// ------------------------------------------------------------------ tracker
+
+void Tracker::access(int res, int64_t lo, int64_t hi, bool write) {
+    if (hi > lo) pend_.push_back({res, lo, hi, write});
+}
+
+void Tracker::commit(int64_t op, int stream, int64_t wait_op[kNumStreams]) {
+    for (int s = 0; s < kNumStreams; ++s) wait_op[s] = -1;
+    // 1) waits: latest conflicting op of every other stream
+    for (const Pending& p : pend_) {
+        for (const Entry& e : res_[p.res]) {
+            if (e.hi <= p.lo || e.lo >= p.hi) continue;
+            if (!(e.write || p.write)) continue;
+            if (e.stream == stream) continue;
+            wait_op[e.stream] = std::max(wait_op[e.stream], e.op);
+        }
+    }
+    // 2) record: a write supersedes everything it overlaps (all of it is
+    //    ordered before this op, by the waits above or by stream order)
+    for (const Pending& p : pend_) {
+        std::vector<Entry>& v = res_[p.res];
+        if (p.write) {
+            std::vector<Entry> keep;
+            keep.reserve(v.size() + 2);
+            for (const Entry& e : v) {
+                if (e.hi <= p.lo || e.lo >= p.hi) { keep.push_back(e); continue; }
+                if (e.lo < p.lo) keep.push_back({e.lo, p.lo, e.op, e.stream, e.write});
+                if (e.hi > p.hi) keep.push_back({p.hi, e.hi, e.op, e.stream, e.write});
+            }
+            keep.push_back({p.lo, p.hi, op, stream, true});
+            v.swap(keep);
+        } else {
+            v.push_back({p.lo, p.hi, op, stream, false});
+        }
+    }
+    pend_.clear();
+}
+
+// ------------------------------------------------------------- op helpers
+
+namespace {
+
+// Physical slot ranges of grid planes [lo, hi) stored from slot0 in a buffer
+// of capacity cap (split at the wrap).
+void add_buf_access(Tracker& tr, int res, int64_t lo, int64_t hi, int64_t slot0, int64_t cap,
+                    bool write) {
+    int64_t n = hi - lo;
+    if (n <= 0) return;
+    int64_t s0 = floor_mod(slot0, cap);
+    int64_t first = std::min(n, cap - s0);
+    tr.access(res, s0, s0 + first, write);
+    if (n > first) tr.access(res, 0, n - first, write);
+}
+
+struct Emitter {
+    RunList& rl;
+    Tracker tr;
+    // resource ids: 0 = host array(s) (each host array gets its own id below)
+    int host_res_base;
+    Emitter(RunList& r, int nres, int host_base) : rl(r), tr(nres), host_res_base(host_base) {}
+
+    int64_t emit(Op& op) {
+        int64_t idx = (int64_t)rl.ops.size();
+        tr.commit(idx, op.pub.stream, op.pub.wait_op);
+        for (int s = 0; s < kNumStreams; ++s)
+            if (op.pub.wait_op[s] >= 0) rl.ops[op.pub.wait_op[s]].waited = true;
+        rl.ops.push_back(op);
+        return idx;
+    }
+    int buf_res(int buf) const { return buf; }           // device buffers: ids 0..nbuf-1
+    int host_res(int arr) const { return host_res_base + arr; }
+};
+
+Op make_op(int kind, int stream, int round, int chunk) {
+    Op op;
+    so2dr_op_t& p = op.pub;
+    p.kind = kind;
+    p.stream = stream;
+    p.round = round;
+    p.chunk = chunk;
+    p.depth = 0;
+    p.edge_lo = p.edge_hi = 0;
+    p.src_buf = p.dst_buf = kHost;
+    p.src_lo = p.src_hi = p.src_slot0 = 0;
+    p.dst_lo = p.dst_hi = p.dst_slot0 = 0;
+    for (int s = 0; s < kNumStreams; ++s) p.wait_op[s] = -1;
+    return op;
+}
+
+struct ChunkGeom {
+    int64_t s, e;      // owned planes
+    int64_t a, b;      // input planes of the round
+    int64_t lo, hi;    // new planes sent this round
+};
+
+ChunkGeom chunk_geom(const Plan& p, int i, int kk) {
+    ChunkGeom g;
+    g.s = p.starts[i];
+    g.e = p.starts[i + 1];
+    int64_t h = (int64_t)p.r * kk;
+    g.a = std::max<int64_t>(0, g.s - h);
+    g.b = std::min<int64_t>(p.n0, g.e + h);
+    g.lo = (i == 0) ? 0 : std::min<int64_t>(p.n0, g.s + h);
+    g.hi = (i == p.d - 1) ? p.n0 : std::min<int64_t>(p.n0, g.e + h);
+    return g;
+}
+
+}  // namespace
+
+// Buffer ids of the out-of-core forward list.
+enum { kBufIn = 0, kBufCoef = 1, kBufX = 2, kBufY = 3, kBufOut0 = 4 };
+constexpr int kNumOut = 2;
+
+// Sizes (planes) of the out-of-core forward buffers for the plan's chunking.
+static void forward_caps(const Plan& p, int64_t* cap_in, int64_t* cap_x, int64_t* cap_y,
+                         int64_t* cap_out) {
+    int64_t pmax = 0;
+    for (int i = 0; i < p.d; ++i) pmax = std::max(pmax, p.starts[i + 1] - p.starts[i]);
+    // Circular input: one chunk's input span plus the next chunk's new planes,
+    // so the host-to-device stream can run one chunk ahead of the kernels.
+    // Spans grow with the round's steps, so the full round (k' = k_off)
+    // bounds the residual one; the pair (last chunk, first chunk of the next
+    // round) is covered by the wrap term.
+    int64_t cin = 0;
+    const int kk = p.k_off;
+    for (int i = 0; i < p.d; ++i) {
+        ChunkGeom g = chunk_geom(p, i, kk);
+        int64_t next_hi = (i + 1 < p.d) ? chunk_geom(p, i + 1, kk).hi
+                                        : (p.rounds > 1 ? p.n0 + chunk_geom(p, 0, kk).hi : g.b);
+        cin = std::max(cin, std::max(g.b - g.a, next_hi - g.a));
+    }
+    int L = (int)launch_depths(p.k_off, p.k_on).size();
+    *cap_in = std::max<int64_t>(cin, 1);
+    *cap_x = (L >= 2) ? pmax + 2 * (int64_t)p.r * std::max(0, p.k_off - p.k_on) : 0;
+    *cap_y = (L >= 3) ? pmax + 2 * (int64_t)p.r * std::max(0, p.k_off - 2 * p.k_on) : 0;
+    *cap_out = pmax;
+}
+
+static size_t forward_arena(const Plan& p, std::vector<Buffer>* out) {
+    int64_t cin, cx, cy, co;
+    forward_caps(p, &cin, &cx, &cy, &co);
+    bool vc = p.kind == SO2DR_VARCOEF_STAR;
+    int64_t cbytes = (p.dtype == SO2DR_F64) ? 8 : 4;
+    std::vector<Buffer> b(kBufOut0 + kNumOut);
+    int64_t off = 0;
+    auto place = [&](int id, int64_t cap, int64_t pb, int nf) {
+        b[id].offset = off;
+        b[id].cap = cap;
+        b[id].plane_bytes = pb;
+        b[id].nfields = nf;
+        off += align_up(cap * pb);
+    };
+    place(kBufIn, cin, p.plane_bytes, 1);
+    place(kBufCoef, vc ? cin : 0, 6 * p.plane_cells * cbytes, 6);
+    place(kBufX, cx, p.plane_bytes, 1);
+    place(kBufY, cy, p.plane_bytes, 1);
+    for (int s = 0; s < kNumOut; ++s) place(kBufOut0 + s, co, p.plane_bytes, 1);
+    off += kAlign;  // device status word
+    if (out) *out = b;
+    return (size_t)off;
+}
+
+bool build_forward_ooc(const Plan& p, RunList& rl, size_t budget) {
+    rl.ops.clear();
+    size_t need = forward_arena(p, &rl.bufs);
+    rl.arena_bytes = need;
+    if (budget && need > budget) return false;
+    const int nbuf = (int)rl.bufs.size();
+    const bool vc = p.kind == SO2DR_VARCOEF_STAR;
+    // host arrays: 0 = grid, 1 = coefficient fields
+    Emitter em(rl, nbuf + 2, nbuf);
+    const int64_t cin = rl.bufs[kBufIn].cap;
+    int64_t g = 0;
+    for (int t = 0; t < p.rounds; ++t) {
+        int kk = round_steps(p.T, p.k_off, t);
+        std::vector<int> depths = launch_depths(kk, p.k_on);
+        int64_t V = (int64_t)t * p.n0;
+        for (int i = 0; i < p.d; ++i, ++g) {
+            ChunkGeom cg = chunk_geom(p, i, kk);
+            // (Algorithm 1) transfer the chunk's new planes to the GPU
+            if (cg.hi > cg.lo) {
+                for (int f = 0; f < (vc ? 2 : 1); ++f) {
+                    int buf = f ? kBufCoef : kBufIn;
+                    Op op = make_op(kOpH2D, kStreamH2D, t, i);
+                    op.host_array = f;
+                    op.nfields = f ? 6 : 1;
+                    op.field_elems = p.n0 * p.plane_cells;
+                    op.pub.src_buf = kHost;
+                    op.pub.src_lo = cg.lo;
+                    op.pub.src_hi = cg.hi;
+                    op.pub.src_slot0 = cg.lo;
+                    op.pub.dst_buf = buf;
+                    op.pub.dst_lo = cg.lo;
+                    op.pub.dst_hi = cg.hi;
+                    op.pub.dst_slot0 = floor_mod(V + cg.lo, cin);
+                    em.tr.access(em.host_res(f), cg.lo, cg.hi, false);
+                    add_buf_access(em.tr, buf, cg.lo, cg.hi, op.pub.dst_slot0, cin, true);
+                    em.emit(op);
+                }
+            }
+            // (Sec. II-B, Sec. IV-B) the chunk's planes [a, b) now sit in the
+            // circular buffer: the lower 2*r*k' of them were sent with the
+            // previous chunk (region sharing), so the k'-step trapezoid runs
+            // without waiting on any neighbour.
+            int64_t in_lo = cg.a, in_hi = cg.b;
+            int src = kBufIn;
+            int64_t src_slot0 = floor_mod(V + cg.a, cin);
+            int m = 0;
+            for (size_t j = 0; j < depths.size(); ++j) {
+                int dl = depths[j];
+                m += dl;
+                bool last = j + 1 == depths.size();
+                int64_t h = (int64_t)p.r * (kk - m);
+                int64_t out_lo = last ? cg.s : std::max<int64_t>(0, cg.s - h);
+                int64_t out_hi = last ? cg.e : std::min<int64_t>(p.n0, cg.e + h);
+                int dst = last ? kBufOut0 + (int)(g % kNumOut) : ((j % 2 == 0) ? kBufX : kBufY);
+                Op op = make_op(kOpKernel, kStreamCompute, t, i);
+                op.fn = kFnStencil;
+                op.pub.depth = dl;
+                op.pub.edge_lo = in_lo == 0;
+                op.pub.edge_hi = in_hi == p.n0;
+                op.pub.src_buf = src;
+                op.pub.src_lo = in_lo;
+                op.pub.src_hi = in_hi;
+                op.pub.src_slot0 = src_slot0;
+                op.pub.dst_buf = dst;
+                op.pub.dst_lo = out_lo;
+                op.pub.dst_hi = out_hi;
+                op.pub.dst_slot0 = 0;
+                int64_t scap = rl.bufs[src].cap;
+                add_buf_access(em.tr, src, in_lo, in_hi, src_slot0, scap, false);
+                if (vc) {
+                    op.aux_buf = kBufCoef;
+                    op.aux_lo = cg.a;
+                    op.aux_slot0 = floor_mod(V + cg.a, cin);
+                    add_buf_access(em.tr, kBufCoef, cg.a, cg.b, op.aux_slot0, cin, false);
+                }
+                add_buf_access(em.tr, dst, out_lo, out_hi, 0, rl.bufs[dst].cap, true);
+                em.emit(op);
+                src = dst;
+                in_lo = out_lo;
+                in_hi = out_hi;
+                src_slot0 = 0;
+            }
+            // (Algorithm 1) transfer the chunk back: its owned interior planes
+            int64_t dlo = std::max<int64_t>(cg.s, p.r), dhi = std::min<int64_t>(cg.e, p.n0 - p.r);
+            if (dhi > dlo) {
+                Op op = make_op(kOpD2H, kStreamD2H, t, i);
+                op.host_array = 0;
+                op.pub.src_buf = src;
+                op.pub.src_lo = dlo;
+                op.pub.src_hi = dhi;
+                op.pub.src_slot0 = dlo - cg.s;
+                op.pub.dst_buf = kHost;
+                op.pub.dst_lo = dlo;
+                op.pub.dst_hi = dhi;
+                op.pub.dst_slot0 = dlo;
+                add_buf_access(em.tr, src, dlo, dhi, dlo - cg.s, rl.bufs[src].cap, false);
+                em.tr.access(em.host_res(0), dlo, dhi, true);
+                em.emit(op);
+            }
+        }
+    }
+    return true;
+}
+
+void build_forward_in_core(const Plan& p, RunList& rl) {
+    rl.ops.clear();
+    const bool vc = p.kind == SO2DR_VARCOEF_STAR;
+    int64_t cbytes = (p.dtype == SO2DR_F64) ? 8 : 4;
+    // buffers: 0 = A, 1 = coefficients, 2 = B
+    rl.bufs.assign(3, Buffer());
+    int64_t off = 0;
+    rl.bufs[0] = {off, p.n0, p.plane_bytes, 1};
+    off += align_up(p.n0 * p.plane_bytes);
+    rl.bufs[1] = {off, vc ? p.n0 : 0, 6 * p.plane_cells * cbytes, 6};
+    off += align_up((vc ? p.n0 : 0) * 6 * p.plane_cells * cbytes);
+    rl.bufs[2] = {off, p.n0, p.plane_bytes, 1};
+    off += align_up(p.n0 * p.plane_bytes);
+    off += kAlign;
+    rl.arena_bytes = (size_t)off;
+    Emitter em(rl, 3 + 2, 3);
+    for (int f = 0; f < (vc ? 2 : 1); ++f) {
+        Op op = make_op(kOpH2D, kStreamH2D, 0, 0);
+        op.host_array = f;
+        op.nfields = f ? 6 : 1;
+        op.field_elems = p.n0 * p.plane_cells;
+        op.pub.src_lo = 0;
+        op.pub.src_hi = p.n0;
+        op.pub.src_slot0 = 0;
+        op.pub.dst_buf = f ? 1 : 0;
+        op.pub.dst_lo = 0;
+        op.pub.dst_hi = p.n0;
+        op.pub.dst_slot0 = 0;
+        em.tr.access(em.host_res(f), 0, p.n0, false);
+        em.tr.access(f ? 1 : 0, 0, p.n0, true);
+        em.emit(op);
+    }
+    int cur = 0;
+    for (int t = 0; t < p.rounds; ++t) {
+        int kk = round_steps(p.T, p.k_off, t);
+        for (int dl : launch_depths(kk, p.k_on)) {
+            int dst = cur == 0 ? 2 : 0;
+            Op op = make_op(kOpKernel, kStreamCompute, t, 0);
+            op.fn = kFnStencil;
+            op.pub.depth = dl;
+            op.pub.edge_lo = op.pub.edge_hi = 1;
+            op.pub.src_buf = cur;
+            op.pub.src_lo = 0;
+            op.pub.src_hi = p.n0;
+            op.pub.dst_buf = dst;
+            op.pub.dst_lo = 0;
+            op.pub.dst_hi = p.n0;
+            if (vc) {
+                op.aux_buf = 1;
+                op.aux_lo = 0;
+                op.aux_slot0 = 0;
+                em.tr.access(1, 0, p.n0, false);
+            }
+            em.tr.access(cur, 0, p.n0, false);
+            em.tr.access(dst, 0, p.n0, true);
+            em.emit(op);
+            cur = dst;
+        }
+    }
+    if (p.n0 - 2 * p.r > 0) {
+        Op op = make_op(kOpD2H, kStreamD2H, p.rounds > 0 ? p.rounds - 1 : 0, 0);
+        op.host_array = 0;
+        op.pub.src_buf = cur;
+        op.pub.src_lo = p.r;
+        op.pub.src_hi = p.n0 - p.r;
+        op.pub.src_slot0 = p.r;
+        op.pub.dst_buf = kHost;
+        op.pub.dst_lo = p.r;
+        op.pub.dst_hi = p.n0 - p.r;
+        op.pub.dst_slot0 = p.r;
+        em.tr.access(cur, p.r, p.n0 - p.r, false);
+        em.tr.access(em.host_res(0), p.r, p.n0 - p.r, true);
+        em.emit(op);
+    }
+}
+
+// ------------------------------------------------------------- cost model
+
+namespace {
+
+// Cell updates the kernels compute for one plan (trapezoids included), and
+// the useful ones.
+void trapezoid_work(const Plan& p, double* computed, double* useful) {
+    double c = 0, u = 0;
+    for (int t = 0; t < p.rounds; ++t) {
+        int kk = round_steps(p.T, p.k_off, t);
+        std::vector<int> depths = launch_depths(kk, p.k_on);
+        for (int i = 0; i < p.d; ++i) {
+            ChunkGeom cg = chunk_geom(p, i, kk);
+            int64_t lo = cg.a, hi = cg.b;
+            int m = 0;
+            for (int dl : depths) {
+                for (int l = 1; l <= dl; ++l) {
+                    int64_t h = (int64_t)p.r * (kk - (m + l));
+                    int64_t zlo = std::max<int64_t>(0, cg.s - h), zhi = std::min<int64_t>(p.n0, cg.e + h);
+                    (void)lo;
+                    (void)hi;
+                    c += (double)(zhi - zlo);
+                }
+                m += dl;
+            }
+            u += (double)(cg.e - cg.s) * kk;
+        }
+    }
+    *computed = c;
+    *useful = u;
+}
+
+double predict_ms(const Plan& p) {
+    double comp, use;
+    trapezoid_work(p, &comp, &use);
+    double cells_plane = (double)p.plane_cells;
+    bool vc = p.kind == SO2DR_VARCOEF_STAR;
+    double in_plane_bytes = (double)p.plane_bytes + (vc ? 6.0 * cells_plane * 4 : 0.0);
+    double host_h2d = (double)p.rounds * p.n0 * in_plane_bytes / (p.bw_h2d * 1e9);
+    double host_d2h = (double)p.rounds * p.interior_planes() * p.plane_bytes / (p.bw_d2h * 1e9);
+    double host = std::max(host_h2d, host_d2h);
+    // in-plane overlapped tiling of a depth-k_on launch (tile 32 x 32)
+    double tile = 32.0, halo = (double)p.r * p.k_on;
+    double inplane = p.ndim == 3 ? ((tile + halo) * (tile + halo)) / (tile * tile)
+                                 : (256.0 + halo) / 256.0;
+    int npts = p.kind == SO2DR_VARCOEF_STAR ? 7 : num_coeffs(p.ndim, p.r, p.kind);
+    double flops = comp * cells_plane * inplane * (2.0 * npts);
+    double rate = (p.dtype == SO2DR_F64) ? 0.6e12 : 25e12;
+    double compute = flops / rate;
+    int L = (int)launch_depths(p.k_off, p.k_on).size();
+    double hbm = (double)p.rounds * p.n0 * p.plane_bytes * (2.0 + 2.0 * L) / (p.bw_hbm * 1e9);
+    double body = std::max(host, std::max(compute, hbm));
+    double fill = body / std::max(1, p.d * p.rounds) * 2.0;
+    return (body + fill) * 1e3;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------- build_plan
+
+static void partition(Plan& p) {
+    int64_t M = p.n0 - 2 * p.r;
+    p.starts.assign(p.d + 1, 0);
+    for (int i = 1; i < p.d; ++i) p.starts[i] = p.r + (M * i) / p.d;
+    p.starts[0] = 0;
+    p.starts[p.d] = p.n0;
+}
+
+// Smallest d >= dmin whose buffers fit (binary search: the buffers shrink as
+// d grows); returns 0 if none.
+static int fit_chunks(Plan& p, int dmin) {
+    int64_t M = p.n0 - 2 * p.r;
+    int dmax = (int)std::max<int64_t>(1, M);
+    int lo = std::max(1, dmin);
+    if (lo > dmax) return 0;
+    auto fits = [&](int d) {
+        p.d = d;
+        partition(p);
+        return !p.budget || forward_arena(p, nullptr) <= p.budget;
+    };
+    if (!fits(dmax)) return 0;
+    if (fits(lo)) return lo;
+    int a = lo, b = dmax;  // fits(a) false, fits(b) true
+    while (b - a > 1) {
+        int m = a + (b - a) / 2;
+        if (fits(m)) b = m; else a = m;
+    }
+    p.d = b;
+    partition(p);
+    return b;
+}
+
+int build_plan(Plan& p, int ndim, const int64_t* dims, int radius, int kind, const double* coeffs,
+               int ncoeffs, int64_t T, int min_chunks, int k_on, int k_off, size_t budget,
+               int dtype, double bw_h2d, double bw_d2h, double bw_hbm, std::string* err) {
+    auto fail = [&](int code, const char* m) { if (err) *err = m; return code; };
+    if (ndim != 2 && ndim != 3) return fail(SO2DR_E_INVAL, "ndim must be 2 or 3");
+    if (!dims) return fail(SO2DR_E_INVAL, "dims is NULL");
+    if (radius < 1 || radius > kMaxRadius) return fail(SO2DR_E_INVAL, "radius must be 1..4");
+    if (kind < SO2DR_STAR || kind > SO2DR_VARCOEF_STAR) return fail(SO2DR_E_INVAL, "unknown stencil kind");
+    if (elem_size(dtype) == 0) return fail(SO2DR_E_INVAL, "unknown storage dtype");
+    if (T < 0) return fail(SO2DR_E_INVAL, "time_steps must be >= 0");
+    if (min_chunks < 1) return fail(SO2DR_E_INVAL, "min_chunks must be >= 1");
+    if (k_on < 0 || k_on > kMaxKon) return fail(SO2DR_E_INVAL, "k_on must be 0..16");
+    if (k_off < 0) return fail(SO2DR_E_INVAL, "k_off must be >= 0");
+    if (kind == SO2DR_BOX && ndim != 2) return fail(SO2DR_E_UNSUPPORTED, "box stencils are provided in 2D");
+    if (kind == SO2DR_VARCOEF_STAR && (ndim != 3 || radius != 1))
+        return fail(SO2DR_E_UNSUPPORTED, "the variable-coefficient stencil is the 3D 7-point star");
+    if (kind == SO2DR_VARCOEF_STAR && (dtype == SO2DR_BF16 || dtype == SO2DR_F16))
+        return fail(SO2DR_E_UNSUPPORTED, "variable coefficients need F32 or F64 storage");
+    if (k_on > p.max_kon)
+        return fail(SO2DR_E_UNSUPPORTED, "k_on exceeds the deepest fused kernel for this stencil");
+    int nc = num_coeffs(ndim, radius, kind);
+    if (kind != SO2DR_VARCOEF_STAR) {
+        if (!coeffs || ncoeffs != nc) return fail(SO2DR_E_INVAL, "coefficient count does not match the stencil");
+        for (int i = 0; i < nc; ++i)
+            if (!std::isfinite(coeffs[i])) return fail(SO2DR_E_INVAL, "non-finite coefficient");
+    }
+    for (int a = 0; a < ndim; ++a)
+        if (dims[a] < 1) return fail(SO2DR_E_INVAL, "dims must be >= 1");
+    if (dims[0] > (int64_t)1 << 31) return fail(SO2DR_E_UNSUPPORTED, "axis 0 longer than 2^31");
+    p.ndim = ndim;
+    p.n0 = dims[0];
+    p.ny = ndim == 3 ? dims[1] : 1;
+    p.nx = ndim == 3 ? dims[2] : dims[1];
+    if (p.nx > (int64_t)1 << 31 || p.ny > (int64_t)1 << 31) return fail(SO2DR_E_UNSUPPORTED, "axis too long");
+    p.r = radius;
+    p.kind = kind;
+    p.dtype = dtype;
+    p.coeffs.assign(coeffs ? coeffs : nullptr, coeffs ? coeffs + std::max(0, nc) : nullptr);
+    p.T = T;
+    p.elem_bytes = elem_size(dtype);
+    p.plane_cells = p.ny * p.nx;
+    p.plane_bytes = p.plane_cells * p.elem_bytes;
+    p.budget = budget;
+    if (bw_h2d > 0) p.bw_h2d = bw_h2d;
+    if (bw_d2h > 0) p.bw_d2h = bw_d2h;
+    if (bw_hbm > 0) p.bw_hbm = bw_hbm;
+    if (p.n0 - 2 * p.r < 1) {
+        // no interior plane: nothing ever changes; a one-chunk plan with no rounds
+        p.k_off = std::max(1, k_off);
+        p.k_on = std::max(1, k_on);
+        p.rounds = 0;
+        p.d = 1;
+        partition(p);
+    } else if (T == 0) {
+        p.k_off = std::max(1, k_off);
+        p.k_on = std::max(1, std::min(k_on ? k_on : 1, p.k_off));
+        p.rounds = 0;
+        p.d = std::min<int64_t>(min_chunks, p.n0 - 2 * p.r);
+        partition(p);
+    } else {
+        std::vector<int> kons, koffs;
+        if (k_on) kons.push_back(k_on);
+        else
+            for (int v : {1, 2, 3, 4, 5, 6, 7, 8, 10, 12, 16})
+                if (v <= p.max_kon) kons.push_back(v);
+        if (k_off) koffs.push_back(k_off);
+        else {
+            for (int64_t v = 1; v <= std::min<int64_t>(T, 64); ++v) koffs.push_back((int)v);
+            for (int64_t v : {80, 96, 112, 128, 160, 192, 256, 320, 384, 512, 640, 1024})
+                if (v < T) koffs.push_back((int)v);
+            if (T > 64) koffs.push_back((int)std::min<int64_t>(T, 1 << 30));
+        }
+        double best = std::numeric_limits<double>::infinity();
+        int bko = 0, bkn = 0, bd = 0;
+        for (int ko : koffs) {
+            for (int kn : kons) {
+                if (kn > ko && koffs.size() > 1) continue;
+                Plan q = p;
+                q.k_off = ko;
+                q.k_on = std::min(kn, ko);
+                q.rounds = (int)((T + ko - 1) / ko);
+                int d = fit_chunks(q, min_chunks);
+                if (!d) continue;
+                double ms = predict_ms(q);
+                if (ms < best) { best = ms; bko = q.k_off; bkn = q.k_on; bd = d; }
+            }
+        }
+        if (!bd) return fail(SO2DR_E_INFEASIBLE, "no chunking fits the device budget");
+        p.k_off = bko;
+        p.k_on = bkn;
+        p.rounds = (int)((T + bko - 1) / bko);
+        p.d = bd;
+        partition(p);
+    }
+    if (!build_forward_ooc(p, p.ooc, p.budget))
+        return fail(SO2DR_E_INFEASIBLE, "no chunking fits the device budget");
+    build_forward_in_core(p, p.ic);
+    int64_t cin, cx, cy, co;
+    forward_caps(p, &cin, &cx, &cy, &co);
+    p.ring_planes = cin;
+    double comp = 0, use = 0;
+    if (p.rounds > 0) trapezoid_work(p, &comp, &use);
+    p.redundancy = use > 0 ? comp / use - 1.0 : 0.0;
+    return SO2DR_OK;
+}
+
+}  // namespace so2dr

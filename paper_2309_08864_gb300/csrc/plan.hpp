@@ -1,0 +1,131 @@
+// plan.hpp -- host-side plan of the SO2DR pipeline (no CUDA calls).
+//
+// A plan fixes the chunking along axis 0 (Sec. II-A, Fig. 1b), the rounds and
+// launch-depth sequence of Algorithm 1, the arena layout and, for each run,
+// the complete list of operations (copies and launches) with the cross-stream
+// waits that make it race-free.  The executor (run.cu) only replays the list.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/so2dr.h"
+
+namespace so2dr {
+
+constexpr int kStreamH2D = 0, kStreamCompute = 1, kStreamD2H = 2, kNumStreams = 3;
+constexpr int kOpH2D = 0, kOpKernel = 1, kOpD2H = 2;
+constexpr int kHost = -1;           // buffer id of the host array of a copy
+constexpr int kMaxRadius = 4;
+constexpr int kMaxKon = 16;
+constexpr int kMaxCoeffs = 81;      // (2*4+1)^2 for the 2D box of radius 4
+
+// Kernel programs an op can launch.
+enum KernelFn : int {
+    kFnStencil = 0,     // const-coefficient star/box, or varcoef forward
+    kFnAdjoint = 1,     // transposed varcoef step + coefficient-gradient update
+    kFnResidual = 2,    // lambda_T = u_T - u*, FP64 partial loss
+    kFnDot = 3,         // FP64 partial inner products
+    kFnReduce = 4,      // FP64 final sum of partials
+    kFnZero = 5,        // clear a buffer region
+};
+
+// One operation, as enqueued.  Extends the public record with what the
+// executor needs and the introspection API does not expose.
+struct Op {
+    so2dr_op_t pub;
+    int fn = kFnStencil;
+    int host_array = 0;     // copies: which host array (see the run's array table)
+    int64_t field_elems = 0;// copies: element offset between fields (multi-field copies)
+    int nfields = 1;        // copies: number of fields moved by this op
+    int64_t buf_field_stride = 0; // copies/kernels: bytes between fields inside a buffer
+    int aux_buf = -1;       // kernels: extra buffer (coefficients, states, gradients)
+    int64_t aux_lo = 0, aux_slot0 = 0;
+    int aux2_buf = -1;
+    int64_t aux2_lo = 0, aux2_slot0 = 0;
+    int64_t arg0 = 0, arg1 = 0;  // kernel-specific integers
+    bool waited = false;    // some later op waits on this op's completion event
+};
+
+struct Buffer {
+    int64_t offset = 0;     // bytes from the arena base
+    int64_t cap = 0;        // planes
+    int64_t plane_bytes = 0;// bytes per plane (x fields)
+    int nfields = 1;
+};
+
+// Interval access tracker used while emitting ops: finds, for each new op,
+// the latest conflicting op of every other stream.
+class Tracker {
+public:
+    explicit Tracker(int nres) : res_(nres) {}
+    // Adds one access of the op being built; call for each access, then commit().
+    void access(int res, int64_t lo, int64_t hi, bool write);
+    // Fills wait_op[] for op index `op` on `stream`, records its accesses.
+    void commit(int64_t op, int stream, int64_t wait_op[kNumStreams]);
+
+private:
+    struct Entry { int64_t lo, hi, op; int stream; bool write; };
+    struct Pending { int res; int64_t lo, hi; bool write; };
+    std::vector<std::vector<Entry>> res_;
+    std::vector<Pending> pend_;
+};
+
+struct RunList {
+    std::vector<Op> ops;
+    std::vector<Buffer> bufs;
+    size_t arena_bytes = 0;
+};
+
+struct Plan {
+    // problem
+    int ndim = 3;
+    int64_t n0 = 0, ny = 1, nx = 1;   // axis 0, then the in-plane extents (ny = 1 in 2D)
+    int r = 1, kind = SO2DR_STAR, dtype = SO2DR_F32;
+    std::vector<double> coeffs;
+    int64_t T = 0;
+    // schedule
+    int k_off = 1, k_on = 1, rounds = 0, d = 1;
+    std::vector<int64_t> starts;      // d + 1 entries, partition of [0, n0)
+    int64_t elem_bytes = 4, plane_cells = 0, plane_bytes = 0;
+    size_t budget = 0;
+    int64_t ring_planes = 0;
+    // cost-model inputs
+    double bw_h2d = 171.0, bw_d2h = 171.0, bw_hbm = 6781.0;
+    // op lists of a forward run
+    RunList ooc, ic;
+    double redundancy = 0.0;
+    int max_kon = kMaxKon;            // deepest fused launch the kernel supports
+
+    int64_t interior_planes() const { return n0 - 2 * r; }
+    double cell_updates() const;
+};
+
+// Builds a plan; returns SO2DR_OK or an error code (message in *err).
+int build_plan(Plan& p, int ndim, const int64_t* dims, int radius, int kind, const double* coeffs,
+               int ncoeffs, int64_t T, int min_chunks, int k_on, int k_off, size_t budget,
+               int dtype, double bw_h2d, double bw_d2h, double bw_hbm, std::string* err);
+
+// Launch-depth sequence of a round of k steps with k_on-step kernels
+// (Algorithm 1: floor(k/k_on) k_on-step launches, then one (k mod k_on)-step).
+std::vector<int> launch_depths(int k, int k_on);
+
+// Steps of round t (the last round runs n mod k_off when that is non-zero).
+int round_steps(int64_t T, int k_off, int t);
+
+int64_t elem_size(int dtype);
+int num_coeffs(int ndim, int radius, int kind);
+
+// Forward op list for the given chunking.  Fills rl; returns false if the
+// buffers do not fit `budget` (budget 0 = unlimited).
+bool build_forward_ooc(const Plan& p, RunList& rl, size_t budget);
+void build_forward_in_core(const Plan& p, RunList& rl);
+
+// Adjoint pipeline pieces (built per call; see run.cu).
+struct AdjLayout {
+    RunList fwd_store;   // forward that also writes every level (recompute)
+};
+
+}  // namespace so2dr

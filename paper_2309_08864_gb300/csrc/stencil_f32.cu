@@ -1,0 +1,5 @@
+// stencil_f32.cu -- temporal-blocking kernels for f32 storage.
+#define STORAGE_T float
+#define STORAGE_HAS_VARCOEF 1
+#define LAUNCH_FN launch_stencil_f32
+#include "stencil_inst.inc"

@@ -1,0 +1,5 @@
+// stencil_f64.cu -- temporal-blocking kernels for f64 storage.
+#define STORAGE_T double
+#define STORAGE_HAS_VARCOEF 1
+#define LAUNCH_FN launch_stencil_f64
+#include "stencil_inst.inc"

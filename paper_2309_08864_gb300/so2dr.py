@@ -1,0 +1,267 @@
+"""Thin Python binding of the SO2DR C ABI (include/so2dr.h).
+
+Argument marshalling only: every step of the stencil path runs in libso2dr.so
+(CUDA kernels for sm_103a plus the C++ planner and executor).  PyTorch supplies
+the device arena, the three streams and pinned host tensors.  There is no CPU
+fallback: if the library is missing or fails to load, every call raises.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+F64, F32, BF16, F16 = 0, 1, 2, 3
+STAR, BOX, VARCOEF_STAR = 0, 1, 2
+DTYPES = {"f64": F64, "f32": F32, "bf16": BF16, "f16": F16}
+KINDS = {"star": STAR, "box": BOX, "varcoef": VARCOEF_STAR}
+
+OK, E_INVAL, E_INFEASIBLE, E_NOT_BOUND, E_CUDA, E_TIMEOUT, E_DEVICE_CHECK, E_NOMEM, \
+    E_NOT_PINNED, E_UNSUPPORTED = 0, -1, -2, -3, -4, -5, -6, -7, -8, -9
+
+SYMBOLS = ["so2dr_plan", "so2dr_plan_ex", "so2dr_plan_info", "so2dr_plan_chunks", "so2dr_plan_ops",
+           "so2dr_plan_buffers", "so2dr_bind", "so2dr_run", "so2dr_adjoint", "so2dr_loss", "so2dr_dot",
+           "so2dr_destroy", "so2dr_strerror", "so2dr_last_error", "so2dr_abi_version"]
+
+
+class So2drError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s (%d): %s" % (_strerror(code), code, msg))
+        self.code = code
+
+
+class PlanInfo(ctypes.Structure):
+    _fields_ = [("ndim", ctypes.c_int), ("dims", ctypes.c_int64 * 3), ("radius", ctypes.c_int),
+                ("kind", ctypes.c_int), ("dtype", ctypes.c_int), ("time_steps", ctypes.c_int64),
+                ("k_off", ctypes.c_int), ("k_on", ctypes.c_int), ("rounds", ctypes.c_int),
+                ("chunks", ctypes.c_int), ("n_streams", ctypes.c_int),
+                ("max_chunk_planes", ctypes.c_int64), ("ring_planes", ctypes.c_int64),
+                ("plane_bytes", ctypes.c_int64), ("arena_bytes", ctypes.c_size_t),
+                ("arena_bytes_in_core", ctypes.c_size_t), ("host_workspace_bytes", ctypes.c_size_t),
+                ("ops_per_run", ctypes.c_int64), ("launches_per_run", ctypes.c_int64),
+                ("h2d_bytes_per_run", ctypes.c_double), ("d2h_bytes_per_run", ctypes.c_double),
+                ("cell_updates_per_run", ctypes.c_double), ("redundancy", ctypes.c_double)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("total_ms", ctypes.c_double), ("kernel_ms", ctypes.c_double),
+                ("h2d_ms", ctypes.c_double), ("d2h_ms", ctypes.c_double),
+                ("h2d_bytes", ctypes.c_double), ("d2h_bytes", ctypes.c_double),
+                ("launches", ctypes.c_int64), ("ops", ctypes.c_int64),
+                ("gcells_per_s", ctypes.c_double), ("main_kernel_ms", ctypes.c_double),
+                ("main_kernel_launches", ctypes.c_int64), ("main_kernel_cells", ctypes.c_double)]
+
+
+class OpRec(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("stream", ctypes.c_int), ("round", ctypes.c_int),
+                ("chunk", ctypes.c_int), ("depth", ctypes.c_int), ("edge_lo", ctypes.c_int),
+                ("edge_hi", ctypes.c_int), ("src_buf", ctypes.c_int), ("dst_buf", ctypes.c_int),
+                ("src_lo", ctypes.c_int64), ("src_hi", ctypes.c_int64), ("src_slot0", ctypes.c_int64),
+                ("dst_lo", ctypes.c_int64), ("dst_hi", ctypes.c_int64), ("dst_slot0", ctypes.c_int64),
+                ("wait_op", ctypes.c_int64 * 3)]
+
+
+class BufRec(ctypes.Structure):
+    _fields_ = [("offset_bytes", ctypes.c_int64), ("capacity_planes", ctypes.c_int64)]
+
+
+_lib = None
+
+
+def load_library(path=None):
+    """Loads (building if needed) libso2dr.so.  Raises if it cannot."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if path is None:
+        path = _build.LIB
+        if not os.path.exists(path):
+            raise RuntimeError("libso2dr.so is not built; run __graft_entry__.build() "
+                               "(the CUDA extension is required, there is no fallback)")
+    lib = ctypes.CDLL(path)
+    vp, i64, i64p, dp = ctypes.c_void_p, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64), \
+        ctypes.POINTER(ctypes.c_double)
+    c_int, c_size = ctypes.c_int, ctypes.c_size_t
+    planp = ctypes.POINTER(ctypes.c_void_p)
+    lib.so2dr_plan_ex.argtypes = [planp, c_int, i64p, c_int, c_int, dp, c_int, i64, c_int, c_int,
+                                  c_int, c_size, c_int, ctypes.c_double, ctypes.c_double,
+                                  ctypes.c_double]
+    lib.so2dr_plan.argtypes = [planp, c_int, i64p, c_int, c_int, dp, c_int, i64, c_int, c_int, c_int,
+                               c_size, c_int]
+    lib.so2dr_plan_info.argtypes = [vp, ctypes.POINTER(PlanInfo)]
+    lib.so2dr_plan_chunks.argtypes = [vp, i64p, c_int]
+    lib.so2dr_plan_ops.argtypes = [vp, c_int, ctypes.POINTER(OpRec), i64, i64p]
+    lib.so2dr_plan_buffers.argtypes = [vp, c_int, ctypes.POINTER(BufRec), c_int, ctypes.POINTER(c_int)]
+    lib.so2dr_bind.argtypes = [vp, vp, c_size, ctypes.POINTER(vp), c_int]
+    lib.so2dr_run.argtypes = [vp, vp, vp, c_int, ctypes.POINTER(Stats)]
+    lib.so2dr_adjoint.argtypes = [vp, vp, vp, vp, vp, vp, vp, c_size, c_int, dp, ctypes.POINTER(Stats)]
+    lib.so2dr_loss.argtypes = [vp, vp, vp, vp, vp, c_size, dp]
+    lib.so2dr_dot.argtypes = [vp, vp, vp, i64, c_int, dp]
+    lib.so2dr_destroy.argtypes = [vp]
+    lib.so2dr_destroy.restype = None
+    lib.so2dr_strerror.argtypes = [c_int]
+    lib.so2dr_strerror.restype = ctypes.c_char_p
+    lib.so2dr_last_error.argtypes = []
+    lib.so2dr_last_error.restype = ctypes.c_char_p
+    lib.so2dr_abi_version.restype = c_int
+    _lib = lib
+    return lib
+
+
+def _strerror(code):
+    return load_library().so2dr_strerror(code).decode()
+
+
+def _check(rc):
+    if rc != OK:
+        raise So2drError(rc, load_library().so2dr_last_error().decode())
+
+
+def _ptr(t):
+    """Data pointer of a torch tensor or numpy array."""
+    if t is None:
+        return None
+    if hasattr(t, "data_ptr"):
+        return ctypes.c_void_p(t.data_ptr())
+    return ctypes.c_void_p(t.ctypes.data)
+
+
+def _stats_dict(s):
+    return {k: getattr(s, k) for k, _ in Stats._fields_}
+
+
+class Plan:
+    """A planned SO2DR sweep (so2dr_plan).  Host-only until bind()."""
+
+    def __init__(self, dims, radius=1, kind="star", coeffs=None, time_steps=1, min_chunks=1,
+                 k_on=0, k_off=0, budget_bytes=1 << 30, dtype="f32", link_gbs=(0.0, 0.0),
+                 hbm_gbs=0.0):
+        lib = load_library()
+        self.kind = KINDS[kind] if isinstance(kind, str) else int(kind)
+        self.dtype = DTYPES[dtype] if isinstance(dtype, str) else int(dtype)
+        self.dims = tuple(int(x) for x in dims)
+        c = None if coeffs is None else np.ascontiguousarray(coeffs, dtype=np.float64)
+        self._coeffs = c
+        h = ctypes.c_void_p()
+        d = (ctypes.c_int64 * len(self.dims))(*self.dims)
+        cp = None if c is None else c.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        rc = lib.so2dr_plan_ex(ctypes.byref(h), len(self.dims), d, int(radius), self.kind, cp,
+                               0 if c is None else int(c.size), int(time_steps), int(min_chunks),
+                               int(k_on), int(k_off), int(budget_bytes), self.dtype,
+                               float(link_gbs[0]), float(link_gbs[1]), float(hbm_gbs))
+        _check(rc)
+        self._h = h
+        self._arena = None
+        self._streams = None
+        self._bound_in_core = None
+
+    # ------------------------------------------------------------ lifetime
+    def close(self):
+        if getattr(self, "_h", None):
+            load_library().so2dr_destroy(self._h)
+            self._h = None
+        self._arena = None
+        self._streams = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # ------------------------------------------------------------ introspection
+    @property
+    def info(self):
+        i = PlanInfo()
+        _check(load_library().so2dr_plan_info(self._h, ctypes.byref(i)))
+        out = {k: getattr(i, k) for k, _ in PlanInfo._fields_}
+        out["dims"] = tuple(i.dims)
+        return out
+
+    def chunks(self):
+        n = self.info["chunks"]
+        buf = (ctypes.c_int64 * (n + 1))()
+        _check(load_library().so2dr_plan_chunks(self._h, buf, n + 1))
+        return np.array(buf, dtype=np.int64)
+
+    def ops(self, in_core=False):
+        lib = load_library()
+        n = ctypes.c_int64()
+        _check(lib.so2dr_plan_ops(self._h, int(in_core), None, 0, ctypes.byref(n)))
+        arr = (OpRec * n.value)()
+        _check(lib.so2dr_plan_ops(self._h, int(in_core), arr, n.value, ctypes.byref(n)))
+        return [{k: (tuple(getattr(o, k)) if k == "wait_op" else getattr(o, k)) for k, _ in OpRec._fields_}
+                for o in arr]
+
+    def buffers(self, in_core=False):
+        lib = load_library()
+        n = ctypes.c_int()
+        _check(lib.so2dr_plan_buffers(self._h, int(in_core), None, 0, ctypes.byref(n)))
+        arr = (BufRec * n.value)()
+        _check(lib.so2dr_plan_buffers(self._h, int(in_core), arr, n.value, ctypes.byref(n)))
+        return [(b.offset_bytes, b.capacity_planes) for b in arr]
+
+    # ------------------------------------------------------------ execution
+    def bind(self, in_core=False, arena=None, streams=None):
+        """Lends a torch device arena and three torch streams to the plan."""
+        import torch
+        info = self.info
+        need = info["arena_bytes_in_core"] if in_core else info["arena_bytes"]
+        need = max(need, info["arena_bytes"])  if not in_core else need
+        if arena is None:
+            arena = torch.empty(max(need, 256), dtype=torch.uint8, device="cuda")
+        if streams is None:
+            streams = [torch.cuda.Stream() for _ in range(3)]
+        hs = (ctypes.c_void_p * 3)(*[ctypes.c_void_p(s.cuda_stream) for s in streams])
+        _check(load_library().so2dr_bind(self._h, ctypes.c_void_p(arena.data_ptr()),
+                                         arena.numel() * arena.element_size(), hs, 3))
+        self._arena = arena
+        self._streams = streams
+        self._bound_in_core = bool(in_core)
+        return self
+
+    def run(self, host_grid, coeff_fields=None, in_core=False, stats=True):
+        """Advances host_grid (pinned CPU tensor of the plan's dtype) in place."""
+        if self._arena is None or (in_core and not self._bound_in_core):
+            self.bind(in_core=in_core)
+        st = Stats()
+        _check(load_library().so2dr_run(self._h, _ptr(host_grid), _ptr(coeff_fields), int(in_core),
+                                         ctypes.byref(st) if stats else None))
+        return _stats_dict(st) if stats else None
+
+    def adjoint(self, u0, coeff_fields, target, grad_u0, grad_coeffs, workspace, checkpoint_every=8,
+                stats=True):
+        if self._arena is None:
+            self.bind()
+        loss = ctypes.c_double()
+        st = Stats()
+        nbytes = workspace.numel() * workspace.element_size()
+        _check(load_library().so2dr_adjoint(self._h, _ptr(u0), _ptr(coeff_fields), _ptr(target),
+                                            _ptr(grad_u0), _ptr(grad_coeffs), _ptr(workspace), nbytes,
+                                            int(checkpoint_every), ctypes.byref(loss),
+                                            ctypes.byref(st) if stats else None))
+        return loss.value, (_stats_dict(st) if stats else None)
+
+    def loss(self, u0, coeff_fields, target, workspace):
+        if self._arena is None:
+            self.bind()
+        loss = ctypes.c_double()
+        nbytes = workspace.numel() * workspace.element_size()
+        _check(load_library().so2dr_loss(self._h, _ptr(u0), _ptr(coeff_fields), _ptr(target),
+                                         _ptr(workspace), nbytes, ctypes.byref(loss)))
+        return loss.value
+
+    def dot(self, a, b):
+        if self._arena is None:
+            self.bind()
+        out = ctypes.c_double()
+        dt = F64 if str(a.dtype).endswith("float64") else F32
+        _check(load_library().so2dr_dot(self._h, _ptr(a), _ptr(b), int(a.numel()), dt, ctypes.byref(out)))
+        return out.value

@@ -1,0 +1,132 @@
+"""Planner properties (host only, no GPU): chunking, Algorithm 1's rounds and
+launch depths, transfer coverage, budget fitting and argument errors."""
+import os
+
+import numpy as np
+import pytest
+
+from paper_2309_08864_gb300 import so2dr
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _depths_from_golden(s):
+    if s == "-":
+        return None
+    out = []
+    for part in s.split(","):
+        d, n = part.split("x")
+        out += [int(d)] * int(n)
+    return out
+
+
+def _rounds(ops):
+    return sorted({o["round"] for o in ops})
+
+
+@pytest.mark.parametrize("row", [l.split() for l in open(os.path.join(GOLDEN, "alg1_schedule.txt"))
+                                 if l.strip() and not l.startswith("#")])
+def test_algorithm1_rounds_and_launch_depths(row):
+    n, k_off, k_on, nt, last, full, lastd = row
+    n, k_off, k_on, nt, last = int(n), int(k_off), int(k_on), int(nt), int(last)
+    p = so2dr.Plan((40, 24), 1, "star", [0.2] * 5, n, min_chunks=3, k_on=k_on, k_off=k_off,
+                   budget_bytes=0, dtype="f32")
+    info = p.info
+    assert info["rounds"] == nt
+    ops = p.ops()
+    d = info["chunks"]
+    for t in range(nt):
+        for c in range(d):
+            depths = [o["depth"] for o in ops if o["kind"] == 1 and o["round"] == t and o["chunk"] == c]
+            want = _depths_from_golden(lastd if t == nt - 1 else full)
+            assert depths == want, (t, c, depths, want)
+            assert sum(depths) == (last if t == nt - 1 else k_off)
+
+
+CASES = [
+    dict(dims=(512, 512), r=1, kind="star", T=16, min_chunks=4, k_on=4, k_off=8, budget=1 << 20, dtype="f64"),
+    dict(dims=(64, 20, 18), r=1, kind="star", T=13, min_chunks=5, k_on=3, k_off=5, budget=0, dtype="f32"),
+    dict(dims=(70, 30, 30), r=4, kind="star", T=9, min_chunks=3, k_on=2, k_off=4, budget=0, dtype="f32"),
+    dict(dims=(100, 37), r=2, kind="box", T=11, min_chunks=7, k_on=4, k_off=7, budget=0, dtype="f32"),
+    dict(dims=(33, 9, 11), r=1, kind="varcoef", T=7, min_chunks=4, k_on=2, k_off=3, budget=0, dtype="f32"),
+]
+
+
+def _coeffs(c):
+    from tests.test_oracle_pins import my_offsets
+    if c["kind"] == "varcoef":
+        return None
+    n = len(my_offsets(len(c["dims"]), c["r"], 0 if c["kind"] == "star" else 1))
+    return np.full(n, 1.0 / n)
+
+
+@pytest.mark.parametrize("c", CASES)
+def test_transfers_cover_every_plane_once_per_round(c):
+    p = so2dr.Plan(c["dims"], c["r"], c["kind"], _coeffs(c), c["T"], min_chunks=c["min_chunks"],
+                   k_on=c["k_on"], k_off=c["k_off"], budget_bytes=c["budget"], dtype=c["dtype"])
+    info = p.info
+    n0, r = c["dims"][0], c["r"]
+    ops = p.ops()
+    starts = p.chunks()
+    assert starts[0] == 0 and starts[-1] == n0 and np.all(np.diff(starts) > 0)
+    assert info["chunks"] >= c["min_chunks"]
+    for t in range(info["rounds"]):
+        h2d = np.zeros(n0, int)
+        d2h = np.zeros(n0, int)
+        for o in ops:
+            if o["round"] != t:
+                continue
+            if o["kind"] == 0 and o["dst_buf"] == 0:
+                h2d[o["src_lo"]:o["src_hi"]] += 1
+            if o["kind"] == 2:
+                d2h[o["dst_lo"]:o["dst_hi"]] += 1
+        assert np.all(h2d == 1), "every plane is sent exactly once per round (region sharing)"
+        assert np.all(d2h[r:n0 - r] == 1) and np.all(d2h[:r] == 0) and np.all(d2h[n0 - r:] == 0)
+    # d * N_t host-to-device and device-to-host transfers of the grid (Sec. IV-A)
+    n_h2d = sum(1 for o in ops if o["kind"] == 0 and o["dst_buf"] == 0)
+    n_d2h = sum(1 for o in ops if o["kind"] == 2)
+    assert n_h2d == n_d2h == info["chunks"] * info["rounds"]
+    if c["budget"]:
+        assert info["arena_bytes"] <= c["budget"]
+
+
+def test_budget_raises_chunk_count_and_infeasible_budget_fails():
+    a = so2dr.Plan((256, 64, 64), 1, "star", [0.4] + [0.1] * 6, 16, min_chunks=2, k_on=4, k_off=8,
+                   budget_bytes=0, dtype="f32")
+    b = so2dr.Plan((256, 64, 64), 1, "star", [0.4] + [0.1] * 6, 16, min_chunks=2, k_on=4, k_off=8,
+                   budget_bytes=8 << 20, dtype="f32")
+    assert a.info["chunks"] == 2
+    assert b.info["chunks"] > 2 and b.info["arena_bytes"] <= 8 << 20
+    with pytest.raises(so2dr.So2drError) as e:
+        so2dr.Plan((256, 64, 64), 1, "star", [0.4] + [0.1] * 6, 16, min_chunks=2, k_on=4, k_off=8,
+                   budget_bytes=64 << 10, dtype="f32")
+    assert e.value.code == so2dr.E_INFEASIBLE
+
+
+@pytest.mark.parametrize("kw,code", [
+    (dict(dims=(8, 8, 8, 8)), so2dr.E_INVAL),
+    (dict(radius=0), so2dr.E_INVAL),
+    (dict(radius=5), so2dr.E_INVAL),
+    (dict(coeffs=[0.2] * 4), so2dr.E_INVAL),
+    (dict(time_steps=-1), so2dr.E_INVAL),
+    (dict(min_chunks=0), so2dr.E_INVAL),
+    (dict(k_on=17), so2dr.E_INVAL),
+    (dict(dtype=7), so2dr.E_INVAL),
+    (dict(coeffs=[0.2, 0.2, float("nan"), 0.2, 0.2]), so2dr.E_INVAL),
+])
+def test_invalid_arguments_are_rejected(kw, code):
+    args = dict(dims=(32, 32), radius=1, kind="star", coeffs=[0.2] * 5, time_steps=4, min_chunks=2,
+                k_on=2, k_off=4, budget_bytes=0, dtype="f32")
+    args.update(kw)
+    with pytest.raises(so2dr.So2drError) as e:
+        so2dr.Plan(**args)
+    assert e.value.code == code
+
+
+def test_auto_parameters_fit_the_budget():
+    p = so2dr.Plan((1024, 1024, 1024), 1, "star", [0.4] + [0.1] * 6, 64, min_chunks=8,
+                   budget_bytes=1 << 30, dtype="f32", link_gbs=(171, 171), hbm_gbs=6781)
+    info = p.info
+    assert info["arena_bytes"] <= 1 << 30
+    assert info["chunks"] >= 8
+    assert 1 <= info["k_on"] <= info["k_off"] <= 64

@@ -1,0 +1,84 @@
+"""Replays plans' op lists on the CPU (tests/emulator.py) in random stream
+interleavings allowed by the planner's waits: the out-of-core result must be
+bit-identical to the in-core FP64 oracle (Sec. IV-B: redundant computation and
+region sharing recompute and reuse the same values)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2309_08864_gb300 import inputs, so2dr
+from tests.emulator import replay
+from tests.test_oracle_pins import my_offsets
+
+CASES = [
+    # dims, r, kind, T, min_chunks, k_on, k_off, budget
+    ((48, 40), 1, "star", 16, 4, 4, 8, 0),
+    ((48, 40), 1, "star", 13, 5, 3, 5, 0),
+    ((60, 33), 2, "star", 9, 6, 2, 4, 0),
+    ((70, 12, 14), 1, "star", 11, 7, 4, 8, 0),
+    ((71, 13, 12), 1, "star", 19, 3, 5, 19, 0),
+    ((64, 14, 15), 4, "star", 5, 3, 2, 5, 0),
+    ((50, 30), 3, "box", 7, 4, 2, 3, 0),
+    ((40, 16), 1, "star", 10, 1, 4, 4, 0),      # a single chunk
+    ((40, 16), 1, "star", 10, 38, 4, 10, 0),    # one plane per chunk, P << 2rk
+    ((33, 9, 11), 1, "varcoef", 7, 4, 2, 3, 0),
+    ((512, 512), 1, "star", 16, 4, 4, 8, 1 << 20),  # the 2D Jacobi workload at full size
+]
+
+
+def _setup(dims, r, kind):
+    nd = len(dims)
+    if kind == "varcoef":
+        faces = np.stack([inputs.draw_box(100 + f, dims, a=0.05, b=0.15) for f in range(6)])
+        return None, faces
+    k = 0 if kind == "star" else 1
+    n = len(my_offsets(nd, r, k))
+    c = inputs.draw_box(5, (n,), a=0.5, b=1.5)
+    return c / c.sum(), None
+
+
+@pytest.mark.parametrize("case", CASES)
+def test_out_of_core_replay_is_bit_identical_to_in_core_oracle(case):
+    dims, r, kind, T, dmin, kon, koff, budget = case
+    c, faces = _setup(dims, r, kind)
+    p = so2dr.Plan(dims, r, kind, c, T, min_chunks=dmin, k_on=kon, k_off=koff, budget_bytes=budget,
+                   dtype="f64")
+    u0 = inputs.draw_box(1, dims)
+    if kind == "varcoef":
+        ref = oracle.run_varcoef(u0, faces, T)
+    else:
+        ref = oracle.run(u0, c, r, 0 if kind == "star" else 1, T)
+    seeds = [0, 1, 2] if np.prod(dims) < 100000 else [0]
+    for sd in seeds:
+        got = replay(p, u0, faces, in_core=False, seed=sd)
+        assert np.array_equal(got, ref), "seed %d" % sd
+    for pol in ("h2d_first", "d2h_first"):
+        got = replay(p, u0, faces, in_core=False, policy=pol)
+        assert np.array_equal(got, ref), pol
+    got = replay(p, u0, faces, in_core=True)
+    assert np.array_equal(got, ref)
+
+
+def test_emulator_detects_a_missing_wait():
+    """Sanity check of the emulator itself: dropping the wait that orders a
+    chunk's first kernel after its host-to-device copy must break the result
+    in some interleaving."""
+    dims, r, T = (48, 40), 1, 8
+    c = np.full(5, 0.2)
+    p = so2dr.Plan(dims, r, "star", c, T, min_chunks=4, k_on=4, k_off=8, budget_bytes=0, dtype="f64")
+    ops = p.ops()
+    broken = [dict(o) for o in ops]
+    for o in broken:
+        if o["kind"] == 1:
+            w = list(o["wait_op"])
+            w[0] = -1
+            o["wait_op"] = tuple(w)
+    p.ops = lambda in_core=False: broken if not in_core else ops
+    u0 = inputs.draw_box(1, dims)
+    ref = oracle.run(u0, c, r, 0, T)
+    bad = 0
+    for pol in ("d2h_first", "random"):
+        for sd in range(3):
+            got = replay(p, u0, None, seed=sd, policy=pol)
+            bad += not np.array_equal(got, ref)
+    assert bad > 0
