@@ -1,0 +1,397 @@
+"""Benchmark of the SO2DR out-of-core stencil path on GB300.
+
+Metric: Gcell-updates/s out-of-core on one GB300 (interior cells x time steps
+per second) and its fraction of the roofline max(host-link bytes / measured
+link bandwidth, HBM bytes / measured HBM bandwidth).
+
+Default workload (the 3D 7-point star, FP32, 1024^3 grid of 4 GiB held in
+pinned host memory, 64 time steps, device budget 1 GiB): one benchmark step is
+one so2dr_run over the whole grid -- every round of Algorithm 1: host-to-device
+transfers, the on-chip temporal-blocking kernels over the circular
+region-sharing buffer, device-to-host transfers.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl so2dr|reference]
+                  [--config c2|c1|c3|c4-bf16|c4-f16|c4-f32] [--k-off k] [--k-on k]
+  python bench.py --kernel-case 512 --k-on 4      # in-core kernel run (profiling)
+
+--impl reference times the FP64 CPU oracle (the only reference this method has:
+the paper ships no code) on the host cores, on bounded samples of the same
+workload.  Under torchrun (N > 1) every rank runs its own replica (the path
+does not shard across GPUs); rank 0 prints the line.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+MEASURED = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# host-link bandwidths measured on the GB300 machines with pinned buffers
+# (cudaMemcpyAsync, 4 GiB): host-to-device 211, device-to-host 193, both
+# directions at once 343 GB/s in total.
+LINK_H2D_GBS, LINK_D2H_GBS, LINK_BIDIR_GBS = 211.3, 193.4, 342.7
+
+CONFIGS = {
+    # name: dims, radius, coefficients, steps, dtype, budget, min_chunks
+    "c1": dict(workload="2D 5-point Jacobi FP64 512x512, zero ring, 16 steps, 1 MiB budget",
+               dims=(512, 512), r=1, coeffs="jacobi2d", T=16, dtype="f64", budget=1 << 20,
+               min_chunks=4, k_on=4, k_off=8, zero_ring=True),
+    "c2": dict(workload="3D 7-point star FP32 1024^3 (4 GiB), 64 steps, 1 GiB budget",
+               dims=(1024, 1024, 1024), r=1, coeffs="star7", T=64, dtype="f32", budget=1 << 30,
+               min_chunks=8, k_on=4, k_off=8),
+    "c3": dict(workload="3D 25-point star r=4 FP32 1536^3 (14.5 GB), 32 steps, 4 GiB budget",
+               dims=(1536, 1536, 1536), r=4, coeffs="r4", T=32, dtype="f32", budget=4 << 30,
+               min_chunks=1, k_on=1, k_off=8),
+    "c4-bf16": dict(workload="3D 7-point star BF16 storage 1024^3, 128 steps, 1 GiB budget",
+                    dims=(1024, 1024, 1024), r=1, coeffs="star7", T=128, dtype="bf16",
+                    budget=1 << 30, min_chunks=8, k_on=4, k_off=16),
+    "c4-f16": dict(workload="3D 7-point star FP16 storage 1024^3, 128 steps, 1 GiB budget",
+                   dims=(1024, 1024, 1024), r=1, coeffs="star7", T=128, dtype="f16",
+                   budget=1 << 30, min_chunks=8, k_on=4, k_off=16),
+    "c4-f32": dict(workload="3D 7-point star FP32 storage 1024^3, 128 steps, 1 GiB budget",
+                   dims=(1024, 1024, 1024), r=1, coeffs="star7", T=128, dtype="f32",
+                   budget=1 << 30, min_chunks=8, k_on=4, k_off=8),
+}
+
+
+def coeffs_of(name, inputs):
+    if name == "jacobi2d":
+        return [0.2] * 5
+    if name == "star7":
+        return [0.4] + [0.1] * 6
+    return list(inputs.radius4_star_coeffs())
+
+
+def measured_peaks():
+    try:
+        with open(MEASURED) as f:
+            m = json.load(f)
+        return float(m["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[3:7]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allreduce_max(x, world):
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------ CPU oracle
+
+def oracle_sample(cfg, inputs, steps=None, planes=None):
+    """Times the FP64 oracle on a bounded slab of the workload: `planes`
+    planes of axis 0 (full extent on the other axes) for `steps` time steps.
+    Returns (cell_updates_per_s, cores, sample description)."""
+    import numpy as np
+    import oracle
+    dims = cfg["dims"]
+    nd = len(dims)
+    T = cfg["T"] if steps is None else steps
+    n0 = dims[0] if planes is None else min(planes, dims[0])
+    sub = (n0,) + tuple(dims[1:])
+    u = inputs.draw_box(1, dims, lo=(0,) * nd, hi=sub)
+    c = coeffs_of(cfg["coeffs"], inputs)
+    kind = 0
+    t0 = time.perf_counter()
+    oracle.run(u, c, cfg["r"], kind, T)
+    dt = time.perf_counter() - t0
+    inner = 1
+    for e in sub:
+        inner *= max(0, e - 2 * cfg["r"])
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    desc = "FP64 oracle on a %s slab of the workload (first %d planes), %d steps" % (
+        "x".join(map(str, sub)), n0, T)
+    return inner * T / dt, cores, desc, dt
+
+
+def oracle_sample_planes(cfg, budget_s, inputs):
+    """Slab thickness giving roughly budget_s seconds of oracle work (probe)."""
+    dims = cfg["dims"]
+    probe_planes = min(dims[0], 2 * cfg["r"] + 8)
+    rate, _, _, _ = oracle_sample(cfg, inputs, steps=2, planes=probe_planes)
+    plane_cells = 1
+    for e in dims[1:]:
+        plane_cells *= e
+    want = rate * budget_s / (plane_cells * cfg["T"])
+    return int(max(2 * cfg["r"] + 2, min(dims[0], want)))
+
+
+def run_reference(args, cfg, world, rank):
+    from paper_2309_08864_gb300 import inputs
+    import oracle
+    oracle.build.build()
+    inputs.build()
+    if rank != 0:
+        return 0
+    budget_each = float(os.environ.get("SO2DR_REF_STEP_SECONDS", "8"))
+    planes = oracle_sample_planes(cfg, budget_each, inputs)
+    rates = []
+    for i in range(args.warmup + args.steps):
+        rate, cores, desc, dt = oracle_sample(cfg, inputs, planes=planes)
+        if i >= args.warmup:
+            rates.append(rate)
+    value = statistics.mean(rates) / 1e9
+    line = {"impl": "reference", "metric": "Gcell-updates/s out-of-core on 1 GB300; % of max(host-link, HBM) roofline",
+            "value": value, "unit": "Gcell/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic (SplitMix64-seeded)",
+            "config": {"workload": cfg["workload"], "sample": desc},
+            "cpu_baseline": {"value": value, "unit": "Gcell/s", "cores": cores, "kind": "oracle", "sample": desc},
+            "e2e": {"value": value, "unit": "Gcell/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ GPU path
+
+def make_input(cfg, inputs, so2dr, torch):
+    import numpy as np
+    dims = cfg["dims"]
+    dt = cfg["dtype"]
+    if dt in ("f32", "bf16", "f16"):
+        u = inputs.draw_box(1, dims, as_f32=True)
+        if dt == "bf16":
+            t = torch.from_numpy(u).to(torch.bfloat16)
+        elif dt == "f16":
+            t = torch.from_numpy(u).to(torch.float16)
+        else:
+            t = torch.from_numpy(u)
+    else:
+        u = inputs.draw_box(1, dims)
+        if cfg.get("zero_ring"):
+            inputs.zero_ring(u, cfg["r"])
+        t = torch.from_numpy(u)
+    if cfg.get("zero_ring") and dt != "f64":
+        inputs.zero_ring(t.numpy(), cfg["r"])
+    return t.pin_memory()
+
+
+def run_kernel_case(args):
+    """In-core run of the temporal-blocking kernel on an n^3 FP32 grid (the
+    shape the ncu captures use)."""
+    import torch
+    from paper_2309_08864_gb300 import inputs, so2dr
+    n = args.kernel_case
+    r = args.radius
+    coeffs = [0.4] + [0.1] * 6 if r == 1 else list(inputs.radius4_star_coeffs())
+    kon = args.k_on or 4
+    T = kon * max(1, args.launches)
+    u = torch.from_numpy(inputs.draw_box(1, (n, n, n), as_f32=True)).pin_memory()
+    plan = so2dr.Plan((n, n, n), r, "star", coeffs, T, min_chunks=1, k_on=kon, k_off=T, budget_bytes=0,
+                      dtype="f32")
+    for _ in range(max(1, args.warmup) + args.steps):
+        st = plan.run(u, in_core=True)
+    print(json.dumps({"kernel_case": n, "radius": r, "k_on": kon, "launches": st["launches"],
+                      "kernel_ms_per_launch": st["kernel_ms"] / st["launches"],
+                      "alg_GBs": 2 * 4 * n ** 3 / (st["kernel_ms"] / st["launches"] * 1e-3) / 1e9}))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="so2dr", choices=["so2dr", "reference"])
+    ap.add_argument("--config", default="c2", choices=sorted(CONFIGS))
+    ap.add_argument("--k-off", type=int, default=None)
+    ap.add_argument("--k-on", type=int, default=None)
+    ap.add_argument("--kernel-case", type=int, default=0)
+    ap.add_argument("--radius", type=int, default=1)
+    ap.add_argument("--launches", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    cfg = dict(CONFIGS[args.config])
+    if args.k_off is not None:
+        cfg["k_off"] = args.k_off
+    if args.k_on is not None:
+        cfg["k_on"] = args.k_on
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        return run_reference(args, cfg, world, rank)
+
+    import torch
+    from paper_2309_08864_gb300 import inputs, so2dr
+    torch.cuda.set_device(local)
+    if args.kernel_case:
+        return run_kernel_case(args)
+
+    hbm_peak, peak_kind = measured_peaks()
+    coeffs = coeffs_of(cfg["coeffs"], inputs)
+    host = make_input(cfg, inputs, so2dr, torch)
+    plan = so2dr.Plan(cfg["dims"], cfg["r"], "star", coeffs, cfg["T"], min_chunks=cfg["min_chunks"],
+                      k_on=cfg["k_on"], k_off=cfg["k_off"], budget_bytes=cfg["budget"], dtype=cfg["dtype"],
+                      link_gbs=(LINK_BIDIR_GBS / 2, LINK_BIDIR_GBS / 2), hbm_gbs=hbm_peak)
+    info = plan.info
+    plan.bind()
+    for _ in range(args.warmup):
+        plan.run(host)
+    torch.cuda.synchronize()
+    barrier(world)
+    clocks = ClockSampler(local)
+    clocks.start()
+    stats = []
+    walls = []
+    t_all = time.perf_counter()
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        stats.append(plan.run(host))   # synchronous: joins every stream before returning
+        walls.append(time.perf_counter() - t0)
+    torch.cuda.synchronize()
+    t_all = time.perf_counter() - t_all
+    barrier(world)
+    clk = clocks.stop()
+
+    dev_ms = sum(s["total_ms"] for s in stats)
+    dev_ms_max = allreduce_max(dev_ms, world)
+    wall_max = allreduce_max(sum(walls), world)
+    cells = info["cell_updates_per_run"]
+    value = world * cells * args.steps / (dev_ms_max * 1e-3) / 1e9
+    e2e = world * cells * args.steps / wall_max / 1e9
+    # roofline of the dominant kernel (the k_on-deep launches)
+    mk_ms = sum(s["main_kernel_ms"] for s in stats)
+    mk_n = sum(s["main_kernel_launches"] for s in stats)
+    mk_cells = sum(s["main_kernel_cells"] for s in stats)
+    b = {"f64": 8, "f32": 4, "bf16": 2, "f16": 2}[cfg["dtype"]]
+    alg_bytes_per_launch = 2 * b * mk_cells / max(1, mk_n)
+    avg_launch_s = mk_ms / max(1, mk_n) * 1e-3
+    achieved = alg_bytes_per_launch / avg_launch_s / 1e9 if mk_n else 0.0
+    # whole-path roofline: max(host-link time, HBM time) of the algorithmic bytes
+    R, L = info["rounds"], -(-info["k_off"] // info["k_on"])
+    Nb = 1
+    for e in cfg["dims"]:
+        Nb *= e
+    Nb *= b
+    b_host = 2.0 * Nb * R
+    b_hbm = Nb * R * (2.0 + 2.0 * L)
+    t_roof = max(b_host / (LINK_BIDIR_GBS * 1e9), b_hbm / (hbm_peak * 1e9))
+    t_meas = dev_ms / args.steps * 1e-3
+    h2d = stats[-1]["h2d_bytes"]
+    d2h = stats[-1]["d2h_bytes"]
+    line = {
+        "metric": "Gcell-updates/s out-of-core on 1 GB300; % of max(host-link, HBM) roofline",
+        "value": value, "unit": "Gcell/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": dev_ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": cfg["dtype"], "data": "synthetic (SplitMix64-seeded)",
+        "config": {"workload": cfg["workload"], "dims": list(cfg["dims"]), "radius": cfg["r"],
+                   "time_steps": cfg["T"], "device_budget_bytes": cfg["budget"], "k_off": info["k_off"],
+                   "k_on": info["k_on"], "chunks": info["chunks"], "rounds": R,
+                   "ring_planes": info["ring_planes"], "arena_bytes": info["arena_bytes"],
+                   "redundancy": info["redundancy"], "parallelism": "replicas" if world > 1 else "1 GPU",
+                   "l2": "inputs larger than L2 (grid of %.1f GiB vs 126 MB L2)" % (Nb / 2 ** 30)},
+        "path_roofline": {"bound": "host-link" if b_host / LINK_BIDIR_GBS >= b_hbm / hbm_peak else "hbm",
+                          "t_roof_ms": t_roof * 1e3, "t_measured_ms": t_meas * 1e3, "frac": t_roof / t_meas,
+                          "host_bytes": b_host, "hbm_bytes": b_hbm, "link_bidir_gbs": LINK_BIDIR_GBS,
+                          "hbm_gbs": hbm_peak,
+                          "measured_link_gbs": {"h2d": h2d / (stats[-1]["h2d_ms"] * 1e-3) / 1e9,
+                                                "d2h": d2h / (stats[-1]["d2h_ms"] * 1e-3) / 1e9,
+                                                "both_during_run": (h2d + d2h) / (stats[-1]["total_ms"] * 1e-3) / 1e9}},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                     "frac": achieved / hbm_peak, "traffic": None,
+                     "kernel": "star3d_fast_kernel (k_on-step TB launch)", "peak_kind": peak_kind + " (burst)",
+                     "avg_launch_ms": avg_launch_s * 1e3, "launches": mk_n},
+        "e2e": {"value": e2e, "unit": "Gcell/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": int(sum(s["launches"] for s in stats)),
+        "clocks": clk,
+        "stage_ms_per_step": {"kernel": sum(s["kernel_ms"] for s in stats) / args.steps,
+                              "h2d": sum(s["h2d_ms"] for s in stats) / args.steps,
+                              "d2h": sum(s["d2h_ms"] for s in stats) / args.steps},
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        from paper_2309_08864_gb300 import inputs as _inp
+        import oracle
+        oracle.build.build()
+        planes = oracle_sample_planes(cfg, 15.0, _inp)
+        rate, cores, desc, dt = oracle_sample(cfg, _inp, planes=planes)
+        line["cpu_baseline"] = {"value": rate / 1e9, "unit": "Gcell/s", "cores": cores, "kind": "oracle",
+                                "sample": desc + " (%.1f s)" % dt}
+    plan.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

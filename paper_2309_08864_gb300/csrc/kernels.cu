@@ -1,5 +1,8 @@
 // kernels.cu -- launch geometry and dtype dispatch of the stencil kernel.
 #include "kernels.hpp"
+#include "star3d_fast.cuh"
+
+#include <cstdlib>
 
 namespace so2dr {
 
@@ -16,10 +19,45 @@ int tile_edge(int H) {
 }
 }  // namespace
 
-LaunchShape stencil_launch_shape(int shape, int r, int depth, int64_t ny, int64_t nx, int csize) {
+bool fast_star3d_supported(int r, int depth) {
+    return (r == 1 && depth >= 1 && depth <= 4) || (r == 2 && depth >= 1 && depth <= 2) ||
+           ((r == 3 || r == 4) && depth == 1);
+}
+
+namespace {
+template <int R, int K> void fast_shape(LaunchShape& ls, int64_t ny, int64_t nx, int esize) {
+    using S = FastShape<R, K>;
+    ls.lx = S::LX;
+    ls.ly = S::LYT;
+    ls.tx = S::TX;
+    ls.ty = S::TY;
+    ls.block = dim3(S::NW * 32, 1, 1);
+    ls.smem = esize == 4 ? S::template smem<4>() : S::template smem<2>();
+    ls.grid = dim3((unsigned)((nx + S::TX - 1) / S::TX), (unsigned)((ny + S::TY - 1) / S::TY), 1);
+    ls.ok = ls.grid.y <= 65535;
+    ls.fast = true;
+}
+}  // namespace
+
+LaunchShape stencil_launch_shape(int shape, int r, int depth, int64_t ny, int64_t nx, int csize, int esize) {
     LaunchShape ls;
     ls.ok = false;
+    ls.fast = false;
     if (depth < 1) return ls;
+    if (shape == kStar3D && csize == 4 && nx % 4 == 0 && fast_star3d_supported(r, depth) &&
+        !std::getenv("SO2DR_GENERIC_KERNEL")) {
+        switch (r * 16 + depth) {
+            case 17: fast_shape<1, 1>(ls, ny, nx, esize); break;
+            case 18: fast_shape<1, 2>(ls, ny, nx, esize); break;
+            case 19: fast_shape<1, 3>(ls, ny, nx, esize); break;
+            case 20: fast_shape<1, 4>(ls, ny, nx, esize); break;
+            case 33: fast_shape<2, 1>(ls, ny, nx, esize); break;
+            case 34: fast_shape<2, 2>(ls, ny, nx, esize); break;
+            case 49: fast_shape<3, 1>(ls, ny, nx, esize); break;
+            case 65: fast_shape<4, 1>(ls, ny, nx, esize); break;
+        }
+        if (ls.ok) return ls;
+    }
     int H = r * depth;
     if (is3d(shape)) {
         ls.lx = ls.ly = tile_edge(H);
@@ -47,7 +85,7 @@ LaunchShape stencil_launch_shape(int shape, int r, int depth, int64_t ny, int64_
 int stencil_max_depth(int shape, int r, int csize) {
     int best = 0;
     for (int d = 1; d <= 16; ++d) {
-        LaunchShape ls = stencil_launch_shape(shape, r, d, 1024, 1024, csize);
+        LaunchShape ls = stencil_launch_shape(shape, r, d, 1024, 1024, csize, csize);
         if (ls.ok) best = d;
     }
     return best;

@@ -14,9 +14,14 @@ struct LaunchShape {
     size_t smem;
     int lx, ly, tx, ty;
     bool ok;
+    bool fast;   // register-streaming 3D star kernel (star3d_fast.cuh)
 };
 
-LaunchShape stencil_launch_shape(int shape, int r, int depth, int64_t ny, int64_t nx, int csize);
+// (R, K) pairs the register-streaming 3D star kernel is instantiated for.
+bool fast_star3d_supported(int r, int depth);
+
+// csize: compute-type bytes; esize: storage-type bytes.
+LaunchShape stencil_launch_shape(int shape, int r, int depth, int64_t ny, int64_t nx, int csize, int esize);
 
 // Largest fused depth the stencil kernel supports for this geometry.
 int stencil_max_depth(int shape, int r, int csize);

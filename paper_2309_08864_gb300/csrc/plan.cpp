@@ -557,7 +557,7 @@ int build_plan(Plan& p, int ndim, const int64_t* dims, int radius, int kind, con
         if (k_on) kons.push_back(k_on);
         else
             for (int v : {1, 2, 3, 4, 5, 6, 7, 8, 10, 12, 16})
-                if (v <= p.max_kon) kons.push_back(v);
+                if (v <= p.max_kon && v <= p.max_kon_auto) kons.push_back(v);
         if (k_off) koffs.push_back(k_off);
         else {
             for (int64_t v = 1; v <= std::min<int64_t>(T, 64); ++v) koffs.push_back((int)v);

@@ -97,7 +97,8 @@ struct Plan {
     // op lists of a forward run
     RunList ooc, ic;
     double redundancy = 0.0;
-    int max_kon = kMaxKon;            // deepest fused launch the kernel supports
+    int max_kon = kMaxKon;            // deepest fused launch the kernels support
+    int max_kon_auto = kMaxKon;       // deepest launch the automatic choice considers
 
     int64_t interior_planes() const { return n0 - 2 * r; }
     double cell_updates() const;

@@ -162,7 +162,7 @@ int enqueue_stencil(so2dr_plan_s* P, const RunList& rl, const Op& op, cudaStream
     const so2dr_op_t& o = op.pub;
     int shape = shape_of(p);
     int csize = p.dtype == SO2DR_F64 ? 8 : 4;
-    LaunchShape ls = stencil_launch_shape(shape, p.r, o.depth, p.ny, p.nx, csize);
+    LaunchShape ls = stencil_launch_shape(shape, p.r, o.depth, p.ny, p.nx, csize, (int)p.elem_bytes);
     if (!ls.ok) return set_error(SO2DR_E_UNSUPPORTED, "fused depth too large for the stencil kernel");
     // host-side argument checks (the kernel trusts them)
     int64_t h = (int64_t)p.r * o.depth;
@@ -295,9 +295,12 @@ int execute(so2dr_plan_s* P, const RunList& rl, char* const* hosts, const int64_
             else {
                 stats->kernel_ms += d;
                 if (o.depth == P->p.k_on && rl.ops[j].fn == kFnStencil) {
+                    // algorithmic cells: the chunk's owned planes (the whole grid in-core)
+                    const Plan& pp = P->p;
+                    int64_t owned = (&rl == &pp.ooc) ? pp.starts[o.chunk + 1] - pp.starts[o.chunk] : pp.n0;
                     stats->main_kernel_ms += d;
                     stats->main_kernel_launches += 1;
-                    stats->main_kernel_cells += (double)(o.dst_hi - o.dst_lo) * (double)P->p.plane_cells;
+                    stats->main_kernel_cells += (double)owned * (double)pp.plane_cells;
                 }
             }
         }
@@ -350,6 +353,14 @@ int so2dr_plan_ex(so2dr_plan_t* out, int ndim, const int64_t* dims, int radius, 
     int rc;
     try {
         P->p.max_kon = maxd;
+        // the automatic choice stays within the register-streaming kernel when
+        // it covers this stencil (the generic kernel is far slower)
+        if (shape == kStar3D && storage != SO2DR_F64 && ndim == 3 && dims && dims[2] % 4 == 0) {
+            int fm = 0;
+            for (int d = 1; d <= kMaxKon; ++d)
+                if (fast_star3d_supported(radius, d)) fm = d;
+            if (fm > 0) P->p.max_kon_auto = fm;
+        }
         rc = build_plan(P->p, ndim, dims, radius, kind, coeffs, ncoeffs, time_steps, min_chunks, k_on, k_off,
                         device_budget_bytes, storage, link_h2d_gbs, link_d2h_gbs, hbm_gbs, &err);
     } catch (const std::bad_alloc&) {

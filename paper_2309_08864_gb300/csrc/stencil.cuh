@@ -142,15 +142,24 @@ __global__ void __launch_bounds__(256) stencil_tb_kernel(const StencilArgs a) {
                     if (!inter) {
                         v = W_(0, 0, 0);
                     } else if (SHAPE == kStar3D) {
-                        // table order: centre; axis 0 (-j,+j); axis 1; axis 2
-                        v = cst[0] * W_(0, 0, 0);
-                        int k = 1;
+                        // streaming order: axis 0 from -R up to -1, centre,
+                        // axis 1 (-j,+j), axis 2 (-j,+j), then axis 0 +1..+R
+                        v = cst[1 + 2 * (R - 1)] * W_(-R, 0, 0);
 #pragma unroll
-                        for (int j = 1; j <= R; ++j) { v = fma_c(cst[k], W_(-j, 0, 0), v); ++k; v = fma_c(cst[k], W_(j, 0, 0), v); ++k; }
+                        for (int j = R - 1; j >= 1; --j) v = fma_c(cst[1 + 2 * (j - 1)], W_(-j, 0, 0), v);
+                        v = fma_c(cst[0], W_(0, 0, 0), v);
 #pragma unroll
-                        for (int j = 1; j <= R; ++j) { v = fma_c(cst[k], W_(0, -j, 0), v); ++k; v = fma_c(cst[k], W_(0, j, 0), v); ++k; }
+                        for (int j = 1; j <= R; ++j) {
+                            v = fma_c(cst[1 + 2 * R + 2 * (j - 1)], W_(0, -j, 0), v);
+                            v = fma_c(cst[2 + 2 * R + 2 * (j - 1)], W_(0, j, 0), v);
+                        }
 #pragma unroll
-                        for (int j = 1; j <= R; ++j) { v = fma_c(cst[k], W_(0, 0, -j), v); ++k; v = fma_c(cst[k], W_(0, 0, j), v); ++k; }
+                        for (int j = 1; j <= R; ++j) {
+                            v = fma_c(cst[1 + 4 * R + 2 * (j - 1)], W_(0, 0, -j), v);
+                            v = fma_c(cst[2 + 4 * R + 2 * (j - 1)], W_(0, 0, j), v);
+                        }
+#pragma unroll
+                        for (int j = 1; j <= R; ++j) v = fma_c(cst[2 + 2 * (j - 1)], W_(j, 0, 0), v);
                     } else if (SHAPE == kStar2D) {
                         v = cst[0] * W_(0, 0, 0);
                         int k = 1;

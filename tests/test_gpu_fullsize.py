@@ -1,0 +1,77 @@
+"""Parity at the full workload sizes, in the launch configuration the benchmark
+times: the out-of-core GPU run is compared, element by element, with the FP64
+oracle on sampled sub-boxes computed from their dependency cones (a cell after
+T steps of a radius-r stencil depends only on cells within r*T of it, the
+fixed ring clipping the cone), and byte for byte with the in-core GPU run."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2309_08864_gb300 import inputs, so2dr
+from tests import gpu_util as gu
+
+pytestmark = pytest.mark.gpu
+
+C2 = dict(dims=(1024, 1024, 1024), r=1, coeffs=[0.4] + [0.1] * 6, T=64, budget=1 << 30, min_chunks=8)
+
+
+def sample_boxes(dims, chunk_starts, rng, n_random=3, w=4):
+    """Corners, chunk boundaries and random spots."""
+    boxes = [((0, 0, 0)), tuple(d - w for d in dims)]
+    for s in chunk_starts[1:-1][:: max(1, len(chunk_starts) // 4)]:
+        boxes.append((max(0, s - w // 2), int(rng.integers(0, dims[1] - w)), dims[2] - w))
+    for _ in range(n_random):
+        boxes.append(tuple(int(rng.integers(0, d - w)) for d in dims))
+    return [(lo, tuple(l + w for l in lo)) for lo in boxes]
+
+
+def cone_check(dims, r, coeffs, T, dtype, host_after, starts, tol, seed=1, n_random=3):
+    rng = np.random.default_rng(0)
+    errs = []
+    c_ref = gu.compute_coeffs(coeffs, dtype)
+    for lo, hi in sample_boxes(dims, starts, rng, n_random):
+        blo, bhi = oracle.cone_box(dims, lo, hi, r * T)
+        ub = inputs.to_storage(inputs.draw_box(seed, dims, blo, bhi), dtype)
+        ref = oracle.run_cone(inputs.storage_to_f64(ub, dtype), c_ref, r, oracle.STAR, T, blo, bhi, dims, lo, hi)
+        got = host_after[tuple(slice(l, h) for l, h in zip(lo, hi))]
+        got = gu.storage_of(got.contiguous(), dtype)
+        e = float(np.max(np.abs(got - ref)) / np.max(np.abs(ref)))
+        errs.append(e)
+        assert e <= tol, (lo, e)
+    return max(errs)
+
+
+def _full_run(dims, r, coeffs, T, dtype, budget, min_chunks, k_on=0, k_off=0, in_core_check=True, seed=1):
+    import torch
+    u = inputs.draw_box(seed, dims, as_f32=True)
+    st = inputs.to_storage(u, dtype) if dtype != so2dr.F32 else u
+    host = gu.pinned_from_storage(st, dtype)
+    ref_copy = host.clone().pin_memory() if in_core_check else None
+    plan = so2dr.Plan(dims, r, "star", coeffs, T, min_chunks=min_chunks, k_on=k_on, k_off=k_off,
+                      budget_bytes=budget, dtype=dtype, link_gbs=(171, 171), hbm_gbs=6781)
+    info = plan.info
+    assert info["arena_bytes"] <= budget
+    plan.run(host)
+    starts = plan.chunks()
+    if in_core_check:
+        ic = so2dr.Plan(dims, r, "star", coeffs, T, min_chunks=1, k_on=info["k_on"], k_off=info["k_off"],
+                        budget_bytes=0, dtype=dtype)
+        ic.run(ref_copy, in_core=True)
+        assert torch.equal(host.view(torch.uint8), ref_copy.view(torch.uint8)), "out-of-core != in-core"
+        ic.close()
+    plan.close()
+    return host, starts, info
+
+
+def test_c2_7pt_1024cubed_fp32_full_size():
+    d = C2
+    host, starts, info = _full_run(d["dims"], d["r"], d["coeffs"], d["T"], so2dr.F32, d["budget"], d["min_chunks"])
+    assert info["chunks"] >= 8
+    cone_check(d["dims"], d["r"], d["coeffs"], d["T"], so2dr.F32, host, starts, 1e-5)
+
+
+def test_c3_25pt_r4_1536cubed_fp32_full_size():
+    dims, r, T = (1536, 1536, 1536), 4, 32
+    c = inputs.radius4_star_coeffs()
+    host, starts, info = _full_run(dims, r, c, T, so2dr.F32, 4 << 30, 1, in_core_check=True)
+    cone_check(dims, r, c, T, so2dr.F32, host, starts, 1e-5, n_random=1)

@@ -66,8 +66,14 @@ def test_jacobi_2d_fp64_full_size():
     assert info["arena_bytes"] <= 1 << 20 and info["chunks"] >= 4
 
 
-@pytest.mark.parametrize("dims,T,dmin,kon,koff", [((72, 70, 66), 12, 5, 4, 8), ((61, 37, 45), 13, 4, 3, 5),
-                                                  ((40, 33, 129), 9, 3, 4, 9), ((30, 24, 24), 5, 1, 5, 5)])
+@pytest.mark.parametrize("dims,T,dmin,kon,koff", [
+    ((72, 70, 132), 12, 5, 4, 8),   # register-streaming kernel, depth 4, two x tiles, ragged y
+    ((61, 37, 44), 13, 4, 3, 5),    # depths 3 and 2 (residual), ragged everything
+    ((40, 33, 260), 9, 3, 2, 9),    # depths 2 and 1, three x tiles
+    ((45, 50, 16), 7, 2, 1, 7),     # depth 1, a single narrow x tile
+    ((72, 70, 66), 12, 5, 4, 8),    # nx % 4 != 0: the generic kernel
+    ((30, 24, 24), 5, 1, 5, 5),     # depth 5: the generic kernel
+])
 def test_star3d_r1_fp32(dims, T, dmin, kon, koff):
     check_case(dims, 1, "star", [0.4] + [0.1] * 6, T, so2dr.F32, dmin, kon, koff, 0)
 
@@ -76,9 +82,15 @@ def test_star3d_r1_fp64():
     check_case((50, 44, 41), 1, "star", [0.4] + [0.1] * 6, 10, so2dr.F64, 4, 4, 8, 0)
 
 
-@pytest.mark.parametrize("dims,T,kon,koff", [((60, 72, 68), 7, 2, 4), ((50, 41, 53), 6, 3, 6)])
+@pytest.mark.parametrize("dims,T,kon,koff", [((60, 72, 68), 7, 2, 4), ((50, 41, 53), 6, 3, 6),
+                                             ((64, 70, 140), 6, 1, 3)])
 def test_star3d_r4_fp32(dims, T, kon, koff):
     check_case(dims, 4, "star", inputs.radius4_star_coeffs(), T, so2dr.F32, 3, kon, koff, 0)
+
+
+@pytest.mark.parametrize("r,kon,koff", [(2, 2, 4), (2, 1, 3), (3, 1, 2)])
+def test_star3d_r2_r3_fp32(r, kon, koff):
+    check_case((52, 45, 136), r, "star", _coeffs(3, r, "star"), 7, so2dr.F32, 3, kon, koff, 0)
 
 
 @pytest.mark.parametrize("r", [1, 2, 3, 4])
