@@ -44,7 +44,7 @@ CONFIGS = {
                min_chunks=4, k_on=4, k_off=8, zero_ring=True),
     "c2": dict(workload="3D 7-point star FP32 1024^3 (4 GiB), 64 steps, 1 GiB budget",
                dims=(1024, 1024, 1024), r=1, coeffs="star7", T=64, dtype="f32", budget=1 << 30,
-               min_chunks=8, k_on=4, k_off=8),
+               min_chunks=8, k_on=4, k_off=12),
     "c3": dict(workload="3D 25-point star r=4 FP32 1536^3 (14.5 GB), 32 steps, 4 GiB budget",
                dims=(1536, 1536, 1536), r=4, coeffs="r4", T=32, dtype="f32", budget=4 << 30,
                min_chunks=1, k_on=1, k_off=8),

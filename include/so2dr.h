@@ -93,7 +93,7 @@ typedef struct {
     int k_on;                /* steps fused in one kernel launch                    */
     int rounds;              /* N_t = ceil(n / k_off)                               */
     int chunks;              /* d                                                   */
-    int n_streams;           /* 3: host-to-device, compute, device-to-host          */
+    int n_streams;           /* 4: host-to-device, compute x2, device-to-host       */
     int64_t max_chunk_planes;/* largest chunk (owned planes)                        */
     int64_t ring_planes;     /* capacity of the circular region-sharing buffer      */
     int64_t plane_bytes;     /* bytes of one stored plane                           */
@@ -133,7 +133,8 @@ typedef struct {
  */
 typedef struct {
     int kind;        /* 0 host-to-device copy, 1 kernel launch, 2 device-to-host copy */
-    int stream;      /* 0 host-to-device, 1 compute, 2 device-to-host                 */
+    int stream;      /* 0 host-to-device, 1 compute (even chunks), 2 device-to-host,
+                        3 compute (odd chunks)                                        */
     int round;
     int chunk;
     int depth;       /* kernels: fused time steps                                     */
@@ -143,7 +144,7 @@ typedef struct {
     int dst_buf;     /* copies: destination buffer; kernels: output buffer            */
     int64_t src_lo, src_hi, src_slot0; /* planes read and where plane src_lo sits     */
     int64_t dst_lo, dst_hi, dst_slot0; /* planes written and where dst_lo sits        */
-    int64_t wait_op[3];/* per stream: index of the latest op of that stream this op
+    int64_t wait_op[4];/* per stream: index of the latest op of that stream this op
                           must wait for (-1 none); same-stream order is implicit     */
 } so2dr_op_t;
 
@@ -199,14 +200,17 @@ int so2dr_plan_buffers(so2dr_plan_t plan, int in_core, so2dr_buffer_t* bufs, int
 /* ------------------------------------------------------------- execution */
 
 /*
- * Lends device memory and streams to the plan (Sec. IV-C fixes three streams:
- * transfers in both directions overlap kernel execution).
+ * Lends device memory and streams to the plan.  Sec. IV-C fixes three streams
+ * so that transfers in both directions overlap kernel execution; here the
+ * streams are host-to-device, compute, device-to-host and a second compute
+ * stream that lets consecutive chunks' launches overlap.
  *   device_arena   caller-owned device memory of at least
  *                  so2dr_plan_info().arena_bytes (or arena_bytes_in_core for
  *                  in-core runs), 256-byte aligned.
- *   cuda_streams   nstreams (3) cudaStream_t handles: host-to-device, compute,
- *                  device-to-host.  NULL entries mean "create private streams"
- *                  (destroyed by so2dr_destroy).
+ * *   cuda_streams   nstreams (3 or 4) cudaStream_t handles: host-to-device,
+ *                  compute, device-to-host[, second compute].  NULL entries (and
+ *                  the fourth stream when nstreams is 3) are created privately
+ *                  and destroyed by so2dr_destroy.
  * Creates the plan's CUDA events on the current device.  Rebinding replaces
  * the previous binding.
  */

@@ -91,6 +91,30 @@ int stencil_max_depth(int shape, int r, int csize) {
     return best;
 }
 
+int stencil_occupancy(int dtype, int shape, int r, int depth, const LaunchShape& ls) {
+    switch (dtype) {
+        case SO2DR_F64: return occupancy_stencil_f64(shape, r, depth, ls);
+        case SO2DR_F32: return occupancy_stencil_f32(shape, r, depth, ls);
+        case SO2DR_BF16: return occupancy_stencil_bf16(shape, r, depth, ls);
+        case SO2DR_F16: return occupancy_stencil_f16(shape, r, depth, ls);
+        default: return 1;
+    }
+}
+
+int choose_segments(int64_t tiles, int64_t nout, int r, int depth, int sms, int occ) {
+    if (tiles <= 0 || nout <= 0 || sms <= 0) return 1;
+    int64_t slots = (int64_t)sms * (occ > 0 ? occ : 1);
+    int best = 1;
+    double best_cost = 0;
+    for (int n = 1; n <= 16 && n <= nout; ++n) {
+        int64_t waves = (tiles * n + slots - 1) / slots;
+        double len = (double)nout / n + 2.0 * r * depth + depth;  // planes one CTA streams
+        double cost = (double)waves * len;
+        if (n == 1 || cost < best_cost * 0.98) { best = n; best_cost = cost; }
+    }
+    return best;
+}
+
 cudaError_t launch_stencil(int dtype, int shape, int r, const StencilArgs& a, const LaunchShape& ls,
                            cudaStream_t s) {
     switch (dtype) {

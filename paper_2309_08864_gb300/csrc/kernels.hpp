@@ -30,7 +30,18 @@ int stencil_max_depth(int shape, int r, int csize);
 cudaError_t launch_stencil(int dtype, int shape, int r, const StencilArgs& a, const LaunchShape& ls,
                            cudaStream_t s);
 
+// CTAs per SM of a launch shape (cudaOccupancyMaxActiveBlocksPerMultiprocessor).
+int stencil_occupancy(int dtype, int shape, int r, int depth, const LaunchShape& ls);
+
+// Axis-0 segments for a launch with `tiles` CTAs per segment, nout output
+// planes and halo r*depth: the count that minimises waves x stream length.
+int choose_segments(int64_t tiles, int64_t nout, int r, int depth, int sms, int occ);
+
 // Per-dtype instantiations (one translation unit each).
+int occupancy_stencil_f64(int shape, int r, int depth, const LaunchShape& ls);
+int occupancy_stencil_f32(int shape, int r, int depth, const LaunchShape& ls);
+int occupancy_stencil_bf16(int shape, int r, int depth, const LaunchShape& ls);
+int occupancy_stencil_f16(int shape, int r, int depth, const LaunchShape& ls);
 cudaError_t launch_stencil_f64(int shape, int r, const StencilArgs& a, const LaunchShape& ls, cudaStream_t s);
 cudaError_t launch_stencil_f32(int shape, int r, const StencilArgs& a, const LaunchShape& ls, cudaStream_t s);
 cudaError_t launch_stencil_bf16(int shape, int r, const StencilArgs& a, const LaunchShape& ls, cudaStream_t s);

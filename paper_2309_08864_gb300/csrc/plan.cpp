@@ -275,7 +275,9 @@ bool build_forward_ooc(const Plan& p, RunList& rl, size_t budget) {
                 int64_t out_lo = last ? cg.s : std::max<int64_t>(0, cg.s - h);
                 int64_t out_hi = last ? cg.e : std::min<int64_t>(p.n0, cg.e + h);
                 int dst = last ? kBufOut0 + (int)(g % kNumOut) : ((j % 2 == 0) ? kBufX : kBufY);
-                Op op = make_op(kOpKernel, kStreamCompute, t, i);
+                // consecutive chunks alternate between two compute streams so
+                // that one chunk's last launch overlaps the next chunk's first
+                Op op = make_op(kOpKernel, (g % 2) ? kStreamCompute2 : kStreamCompute, t, i);
                 op.fn = kFnStencil;
                 op.pub.depth = dl;
                 op.pub.edge_lo = in_lo == 0;

@@ -15,7 +15,8 @@
 
 namespace so2dr {
 
-constexpr int kStreamH2D = 0, kStreamCompute = 1, kStreamD2H = 2, kNumStreams = 3;
+// streams: host-to-device, compute (even chunks), device-to-host, compute (odd chunks)
+constexpr int kStreamH2D = 0, kStreamCompute = 1, kStreamD2H = 2, kStreamCompute2 = 3, kNumStreams = 4;
 constexpr int kOpH2D = 0, kOpKernel = 1, kOpD2H = 2;
 constexpr int kHost = -1;           // buffer id of the host array of a copy
 constexpr int kMaxRadius = 4;

@@ -103,6 +103,8 @@ void so2dr_plan_s::unbind() {
     }
     ev.clear();
     tev.clear();
+    for (auto& row : occ_cache)
+        for (int& v : row) v = 0;
     join.clear();
     for (int s = 0; s < kNumStreams; ++s) { st[s] = nullptr; own[s] = false; }
     arena = nullptr;
@@ -163,6 +165,7 @@ int enqueue_stencil(so2dr_plan_s* P, const RunList& rl, const Op& op, cudaStream
     int shape = shape_of(p);
     int csize = p.dtype == SO2DR_F64 ? 8 : 4;
     LaunchShape ls = stencil_launch_shape(shape, p.r, o.depth, p.ny, p.nx, csize, (int)p.elem_bytes);
+    ls.grid.z = 1;
     if (!ls.ok) return set_error(SO2DR_E_UNSUPPORTED, "fused depth too large for the stencil kernel");
     // host-side argument checks (the kernel trusts them)
     int64_t h = (int64_t)p.r * o.depth;
@@ -203,7 +206,17 @@ int enqueue_stencil(so2dr_plan_s* P, const RunList& rl, const Op& op, cudaStream
     a.tx = ls.tx;
     a.ty = ls.ty;
     a.status = nullptr;
-    for (size_t k = 0; k < p.coeffs.size() && k < (size_t)kMaxCoeffsDev; ++k) a.c[k] = p.coeffs[k];
+    for (size_t k = 0; k < p.coeffs.size() && k < (size_t)kMaxCoeffsDev; ++k) {
+        a.c[k] = p.coeffs[k];
+        a.cf[k] = (float)p.coeffs[k];
+    }
+    if (ls.fast) {
+        // split axis 0 so the grid fills the SMs evenly
+        int& occ = P->occ_cache[1][o.depth];
+        if (!occ) occ = stencil_occupancy(p.dtype, shape, p.r, o.depth, ls);
+        int64_t tiles = (int64_t)ls.grid.x * ls.grid.y;
+        ls.grid.z = (unsigned)choose_segments(tiles, o.dst_hi - o.dst_lo, p.r, o.depth, P->sm_count, occ);
+    }
     cudaError_t e = launch_stencil(p.dtype, shape, p.r, a, ls, s);
     if (e != cudaSuccess) return cuda_fail(e, "stencil launch");
     return SO2DR_OK;
@@ -459,7 +472,7 @@ int so2dr_plan_buffers(so2dr_plan_t P, int in_core, so2dr_buffer_t* bufs, int ma
 
 int so2dr_bind(so2dr_plan_t P, void* device_arena, size_t arena_bytes, void* const* cuda_streams, int nstreams) {
     if (!P || !device_arena) return set_error(SO2DR_E_INVAL, "NULL argument");
-    if (nstreams != kNumStreams) return set_error(SO2DR_E_INVAL, "three streams are required");
+    if (nstreams != 3 && nstreams != 4) return set_error(SO2DR_E_INVAL, "three or four streams are required");
     if (reinterpret_cast<uintptr_t>(device_arena) % 256) return set_error(SO2DR_E_INVAL, "arena must be 256-byte aligned");
     P->unbind();
     int dev = -1;
@@ -472,8 +485,12 @@ int so2dr_bind(so2dr_plan_t P, void* device_arena, size_t arena_bytes, void* con
         return set_error(SO2DR_E_INVAL, "arena is not device memory");
     }
     P->device = dev;
+    if (cudaDeviceGetAttribute(&P->sm_count, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        P->sm_count = 0;
+    }
     for (int s = 0; s < kNumStreams; ++s) {
-        if (cuda_streams && cuda_streams[s]) {
+        if (cuda_streams && s < nstreams && cuda_streams[s]) {
             P->st[s] = static_cast<cudaStream_t>(cuda_streams[s]);
         } else {
             e = cudaStreamCreateWithFlags(&P->st[s], cudaStreamNonBlocking);

@@ -20,6 +20,8 @@ struct so2dr_plan_s {
     std::vector<cudaEvent_t> join;  // start marker + one per stream
     std::vector<cudaEvent_t> tev;   // timing events (2 per op), created on demand
     int device = -1;
+    int sm_count = 0;
+    int occ_cache[2][17] = {};      // CTAs per SM of the fast / generic launch per depth
 
     ~so2dr_plan_s();
     void unbind();

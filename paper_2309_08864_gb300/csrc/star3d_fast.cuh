@@ -4,36 +4,50 @@
 //
 // The on-chip temporal blocking of Sec. III / Sec. IV-A, laid out for sm_103a:
 //  * a CTA owns a 128-wide x tile (32 lanes x float4) and NW*VY rows of y
-//    (one warp per VY rows) and streams the planes of axis 0 through it;
+//    (VY rows per warp) and streams the planes of axis 0 through it; a launch
+//    may also split axis 0 into segments (gridDim.z) so that the grid fills
+//    the SMs evenly;
 //  * each input plane is read from device memory once: cp.async copies
 //    (16-byte vectors, zero-fill outside the grid) stage it one plane ahead in
-//    a double-buffered shared-memory plane that gives the y neighbours; x
-//    neighbours come from warp shuffles;
-//  * every fused level keeps only 2R partial sums per cell in registers: when
-//    the previous level produces plane z', it is added into the targets
-//    z'-R..z'+R (in-plane terms at z'), and target z'-R is complete.  Only
-//    the last level is stored;
-//  * control flow is uniform: the stream runs nin + K*R steps and feeds zeros
-//    beyond the input, which only ever reach targets outside the valid
-//    trapezoid.
-// The computed area shrinks by R per level in y (rows) and x (columns),
-// exactly the compute-area adjustment of Algorithm 1 applied inside a launch.
+//    a double-buffered shared-memory plane; y neighbours come from shared
+//    memory, x neighbours from warp shuffles;
+//  * every fused level keeps 2R partial sums per cell in registers: when the
+//    previous level produces plane z', it is added into the targets
+//    z'-R..z'+R (in-plane terms at z') and target z'-R is complete.  The slot
+//    of a target is fixed by its plane index modulo 2R and the plane loop is
+//    unrolled 2R times, so the ring never moves data;
+//  * levels are pipelined across planes: level l consumes what level l-1
+//    completed in the previous phase, so one barrier per plane suffices;
+//  * every cell is computed as if interior (no per-cell predicates); cells of
+//    the fixed boundary never change, so on completion they take their input
+//    value back from the launch's input buffer (rare, warp-uniform branch);
+//  * control flow is uniform: the stream feeds zeros beyond the input, which
+//    only ever reach targets outside the valid trapezoid.
+// The computed area shrinks by R per level in y and x, the compute-area
+// adjustment of Algorithm 1 applied inside a launch.
 //
 // Per-cell arithmetic order (identical in every launch, chunk and tile):
 //   c(-R e0) u, then FMAs with c(-R+1 e0) ... c(-e0), c(0), c(-e1), c(+e1),
 //   ..., c(-R e1), c(+R e1), c(-e2), c(+e2), ..., c(+e0), ..., c(+R e0).
 #pragma once
 
+#include <type_traits>
+
 #include "stencil.cuh"
+
+// 1: four fused levels run 8 warps x 4 rows (up to 255 registers per thread);
+// 0: 16 warps x 2 rows (128 registers per thread, twice the warps per SM).
+#ifndef SO2DR_K4_VY4
+#define SO2DR_K4_VY4 1
+#endif
 
 namespace so2dr {
 
-// Loaded-tile shape per (R, K): warps along y, VY rows per warp.
+// Loaded-tile shape per (R, K): 16 warps of 2 rows (8 warps for one level);
+// four fused levels keep 4 rows per thread on 8 warps (more registers each).
 template <int R, int K> struct FastShape {
-    // two rows per thread; 16 warps when the launch fuses several levels
-
-    static constexpr int VY = 2;
-    static constexpr int NW = (K == 1) ? 8 : 16;
+    static constexpr int VY = (K >= 4 && SO2DR_K4_VY4) ? 4 : 2;
+    static constexpr int NW = (K == 1 || (K >= 4 && SO2DR_K4_VY4)) ? 8 : 16;
     static constexpr int LX = 128;
     static constexpr int LYT = NW * VY;
     static constexpr int HXA = ((R * K + 3) / 4) * 4;   // x halo, whole float4s
@@ -41,10 +55,10 @@ template <int R, int K> struct FastShape {
     static constexpr int TX = LX - 2 * HXA;
     static constexpr int TY = LYT - 2 * HY;
     static constexpr int INROWS = LYT + 2 * R;
-    template <int ES> static constexpr int smem() { return 2 * INROWS * LX * ES + 2 * (K - 1) * LYT * LX * 4; }
+    static constexpr int LROWS = LYT + 2 * R;           // level planes with R spare rows each side
+    template <int ES> static constexpr int smem() { return 2 * INROWS * LX * ES + 2 * (K - 1) * LROWS * LX * 4; }
 };
 
-// Input rows of a plane are staged with cp.async (zero-fill outside the grid).
 template <typename T> __device__ __forceinline__ void cp_async_vec4(T* sdst, const T* gsrc, bool valid) {
     unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
     int n = valid ? (int)(4 * sizeof(T)) : 0;
@@ -69,20 +83,10 @@ __device__ __forceinline__ float4 lds4(const __half* p) {
     float2 b = __half22float2(*reinterpret_cast<const __half2*>(&raw.y));
     return make_float4(a.x, a.y, b.x, b.y);
 }
+__device__ __forceinline__ float ld1(const float* p) { return *p; }
+__device__ __forceinline__ float ld1(const __nv_bfloat16* p) { return __bfloat162float(*p); }
+__device__ __forceinline__ float ld1(const __half* p) { return __half2float(*p); }
 
-__device__ __forceinline__ float4 ld4(const float* p) { return __ldg(reinterpret_cast<const float4*>(p)); }
-__device__ __forceinline__ float4 ld4(const __nv_bfloat16* p) {
-    uint2 raw = __ldg(reinterpret_cast<const uint2*>(p));
-    float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&raw.x));
-    float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&raw.y));
-    return make_float4(a.x, a.y, b.x, b.y);
-}
-__device__ __forceinline__ float4 ld4(const __half* p) {
-    uint2 raw = __ldg(reinterpret_cast<const uint2*>(p));
-    float2 a = __half22float2(*reinterpret_cast<const __half2*>(&raw.x));
-    float2 b = __half22float2(*reinterpret_cast<const __half2*>(&raw.y));
-    return make_float4(a.x, a.y, b.x, b.y);
-}
 __device__ __forceinline__ void st4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
 __device__ __forceinline__ void st4(__nv_bfloat16* p, float4 v) {
     __nv_bfloat162 a = __floats2bfloat162_rn(v.x, v.y), b = __floats2bfloat162_rn(v.z, v.w);
@@ -107,211 +111,263 @@ __device__ __forceinline__ float f4get(const float4& v, int e) {
 template <int R> __host__ __device__ constexpr int cidx(int axis, int s, int j) {
     return 1 + axis * 2 * R + 2 * (j - 1) + (s > 0 ? 1 : 0);
 }
-
-// One arrival of plane zp of the previous level: v holds its values on my
-// cells, `rows` its smem copy (row 0 = thread-tile row 0 + row_shift; valid
-// rows [rlo, rhi) of the copy).  Updates the 2R partial sums A and returns
-// the completed target zp - R in `done`.
-template <int R, int VY, typename ST>
-__device__ __forceinline__ void level_arrival(float (&A)[2 * R][VY][4], const float (&v)[VY][4],
-                                              const ST* rows, int row_shift, int rlo, int rhi,
-                                              int my_row, int lane, const float* c,
-                                              const unsigned inyx_mask, int64_t zp, int64_t n0,
-                                              float (&done)[VY][4]) {
-    // z-interior flags of the targets zp - R + t, t = 0..2R
-    bool zi[2 * R + 1];
-#pragma unroll
-    for (int t = 0; t <= 2 * R; ++t) {
-        int64_t zt = zp - R + t;
-        zi[t] = zt >= R && zt < n0 - R;
-    }
-    // x neighbours from the adjacent lanes
-    float lft[VY][4], rgt[VY][4];
-#pragma unroll
-    for (int y = 0; y < VY; ++y)
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            lft[y][e] = (e >= 4 - R) ? __shfl_up_sync(0xffffffffu, v[y][e], 1) : 0.f;
-            rgt[y][e] = (e < R) ? __shfl_down_sync(0xffffffffu, v[y][e], 1) : 0.f;
-        }
-    // y neighbours outside my VY rows, from shared memory
-    float4 up[VY][R], dn[VY][R];
-#pragma unroll
-    for (int y = 0; y < VY; ++y)
-#pragma unroll
-        for (int j = 1; j <= R; ++j) {
-            if (y - j < 0) {
-                int r = my_row + y - j + row_shift;
-                r = r < rlo ? rlo : (r >= rhi ? rhi - 1 : r);
-                up[y][j - 1] = lds4(rows + (int64_t)r * 128 + lane * 4);
-            }
-            if (y + j >= VY) {
-                int r = my_row + y + j + row_shift;
-                r = r < rlo ? rlo : (r >= rhi ? rhi - 1 : r);
-                dn[y][j - 1] = lds4(rows + (int64_t)r * 128 + lane * 4);
-            }
-        }
-    float newacc[VY][4];
-#pragma unroll
-    for (int y = 0; y < VY; ++y)
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            const bool cin = (inyx_mask >> (y * 4 + e)) & 1u;
-            const float x = v[y][e];
-            // t = 2R: first contribution to target zp + R (offset -R on axis 0)
-            newacc[y][e] = (cin && zi[2 * R]) ? c[cidx<R>(0, -1, R)] * x : 0.f;
-            // R < t < 2R: offsets -(t-R) on axis 0
-#pragma unroll
-            for (int t = R + 1; t < 2 * R; ++t)
-                if (cin && zi[t]) A[t][y][e] = __fmaf_rn(c[cidx<R>(0, -1, t - R)], x, A[t][y][e]);
-            // t = R: centre and in-plane terms
-            {
-                float s = __fmaf_rn(c[0], x, A[R][y][e]);
-#pragma unroll
-                for (int j = 1; j <= R; ++j) {
-                    float ym = (y - j >= 0) ? v[y - j][e] : f4get(up[y][j - 1], e);
-                    float yp = (y + j < VY) ? v[y + j][e] : f4get(dn[y][j - 1], e);
-                    s = __fmaf_rn(c[cidx<R>(1, -1, j)], ym, s);
-                    s = __fmaf_rn(c[cidx<R>(1, +1, j)], yp, s);
-                }
-#pragma unroll
-                for (int j = 1; j <= R; ++j) {
-                    float xm = (e - j >= 0) ? v[y][e - j] : lft[y][4 + e - j];
-                    float xp = (e + j < 4) ? v[y][e + j] : rgt[y][e + j - 4];
-                    s = __fmaf_rn(c[cidx<R>(2, -1, j)], xm, s);
-                    s = __fmaf_rn(c[cidx<R>(2, +1, j)], xp, s);
-                }
-                A[R][y][e] = (cin && zi[R]) ? s : x;
-            }
-            // 0 <= t < R: offsets +(R-t) on axis 0
-#pragma unroll
-            for (int t = 0; t < R; ++t)
-                if (cin && zi[t]) A[t][y][e] = __fmaf_rn(c[cidx<R>(0, +1, R - t)], x, A[t][y][e]);
-            done[y][e] = A[0][y][e];
-        }
-    // rotate: target zp - R is complete
-#pragma unroll
-    for (int q = 0; q < 2 * R - 1; ++q)
-#pragma unroll
-        for (int y = 0; y < VY; ++y)
-#pragma unroll
-            for (int e = 0; e < 4; ++e) A[q][y][e] = A[q + 1][y][e];
-#pragma unroll
-    for (int y = 0; y < VY; ++y)
-#pragma unroll
-        for (int e = 0; e < 4; ++e) A[2 * R - 1][y][e] = newacc[y][e];
-}
+__host__ __device__ constexpr int pmod(int a, int m) { return ((a % m) + m) % m; }
 
 template <typename T, int R, int K>
-__global__ void __launch_bounds__(FastShape<R, K>::NW * 32, 1) star3d_fast_kernel(const StencilArgs a) {
+struct FastTB {
     using S = FastShape<R, K>;
-    constexpr int VY = S::VY, NW = S::NW, LX = S::LX, LYT = S::LYT, INROWS = S::INROWS;
-    constexpr int RPW = (INROWS + NW - 1) / NW;
-    constexpr int NC = 1 + 6 * R;
-    extern __shared__ float4 smem4[];
-    T* sin = reinterpret_cast<T*>(smem4);                                        // [2][INROWS][LX]
-    float* slev = reinterpret_cast<float*>(smem4) + (2 * INROWS * LX * sizeof(T)) / 4;  // [K-1][2][LYT][LX]
+    static constexpr int VY = S::VY, NW = S::NW, LX = S::LX, LYT = S::LYT, INROWS = S::INROWS;
+    static constexpr int RPW = (INROWS + NW - 1) / NW, W2 = 2 * R, NC = 1 + 6 * R, LROWS = S::LROWS;
 
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int my_row = warp * VY;
-    const int64_t x0 = (int64_t)blockIdx.x * S::TX, y0 = (int64_t)blockIdx.y * S::TY;
-    const int64_t xs = x0 - S::HXA, ys = y0 - S::HY;
-    const int64_t ny = a.ny, nx = a.nx, n0 = a.n0, plane = ny * nx;
-    const T* in = static_cast<const T*>(a.in);
-    T* out = static_cast<T*>(a.out);
+    const StencilArgs& a;
+    T* sin;        // [2][INROWS][LX] staged input planes
+    float* slev;   // [K-1][2][LROWS][LX] completed planes of levels 0..K-2 (R spare rows each side)
+    int rowoff[RPW];   // element offset of each staged row inside a plane
+    unsigned rowok;    // bit i: staged row i lies inside the grid
+    int lane, warp, my_row, n0, olo, ohi;
+    int need_lo, need_hi;  // level L processes arrivals in [need_lo - (K-L)R, need_hi + (K-L)R), clipped at za
+    int xs, ys, ny, nx, gx0, za, zb, slot_next;  // extents and plane indices fit in 32 bits
+    int64_t plane;
+    bool xin, warp_bnd;
+    unsigned inyx;  // bit y*4+e: my cell is an interior cell of the plane
+    const T* in;
+    T* out;
+    float A[K][W2][VY][4];  // 2R partial sums per cell per level
 
-    float c[NC];
-#pragma unroll
-    for (int k = 0; k < NC; ++k) c[k] = (float)a.c[k];
+    __device__ __forceinline__ explicit FastTB(const StencilArgs& args) : a(args) {}
 
-    unsigned inyx = 0;
-#pragma unroll
-    for (int y = 0; y < VY; ++y)
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            int64_t gy = ys + my_row + y, gx = xs + lane * 4 + e;
-            if (gy >= R && gy < ny - R && gx >= R && gx < nx - R) inyx |= 1u << (y * 4 + e);
-        }
-
-    float A[K][2 * R][VY][4];
-#pragma unroll
-    for (int l = 0; l < K; ++l)
-#pragma unroll
-        for (int q = 0; q < 2 * R; ++q)
-#pragma unroll
-            for (int y = 0; y < VY; ++y)
-#pragma unroll
-                for (int e = 0; e < 4; ++e) A[l][q][y][e] = 0.f;
-
-    const int64_t gx0 = xs + lane * 4;
-    const bool xin = gx0 >= 0 && gx0 < nx;  // nx % 4 == 0: a vector is all in or all out
-    // stage input plane z (zeros past the input or outside the grid) in buffer b
-    auto stage_plane = [&](int64_t z, int b) {
-        const bool zin = z < a.in_hi;
-        const int64_t slot = zin ? (a.in_slot0 + (z - a.in_lo)) % a.in_cap : 0;
-        const T* base = in + slot * plane;
-        T* sb = sin + b * INROWS * LX;
+    // input plane z -> buffer b (zeros past zb or outside the grid)
+    __device__ __forceinline__ void stage_plane(int z, int b) {
+        if (z >= zb) return;  // past the input: the buffer keeps stale data that only phantom targets see
+        const T* base = in + (int64_t)slot_next * plane;
+        T* sb = sin + b * INROWS * LX + warp * LX + lane * 4;
 #pragma unroll
         for (int i = 0; i < RPW; ++i) {
-            int row = warp + i * NW;
-            if (row < INROWS) {
-                int64_t gy = ys - R + row;
-                bool ok = zin && xin && gy >= 0 && gy < ny;
-                cp_async_vec4(sb + row * LX + lane * 4, ok ? base + gy * nx + gx0 : in, ok);
+            if (warp + i * NW < INROWS) {
+                bool ok = (rowok >> i) & 1u;
+                cp_async_vec4(sb + i * NW * LX, ok ? base + rowoff[i] : in, ok);
             }
         }
         cp_async_commit();
-    };
+        if (++slot_next == a.in_cap) slot_next = 0;
+    }
 
-    const int64_t nin = a.in_hi - a.in_lo;
-    const int64_t nsteps = nin + (int64_t)K * R;
-    stage_plane(a.in_lo, 0);
-    for (int64_t s = 0; s < nsteps; ++s) {
-        const int64_t zin = a.in_lo + s;
-        const int buf = (int)(s & 1);
-        const T* sbuf = sin + buf * INROWS * LX;
-        cp_async_wait_all();
-        __syncthreads();  // plane zin staged by everyone; step s-1 fully done
-        if (s + 1 < nsteps) stage_plane(zin + 1, buf ^ 1);
-        // ---- level 1: arrival of input plane zin
-        float v[VY][4], done[VY][4];
+    // one arrival at level L of plane zp (phase PH = (zp - za) mod 2R); rows
+    // is the arrival plane's smem copy, tile row t at row t + shift (rows
+    // -R..LYT+R-1 of the tile exist; those outside the tile hold garbage that
+    // only reaches cells outside the level's valid area)
+    template <int L, int PH, typename ST>
+    __device__ __forceinline__ void arrive(const float (&v)[VY][4], const ST* rows, int shift,
+                                           float (&done)[VY][4]) {
+        float lft[VY][4], rgt[VY][4];
+#pragma unroll
+        for (int y = 0; y < VY; ++y)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                lft[y][e] = (e >= 4 - R) ? __shfl_up_sync(0xffffffffu, v[y][e], 1) : 0.f;
+                rgt[y][e] = (e < R) ? __shfl_down_sync(0xffffffffu, v[y][e], 1) : 0.f;
+            }
+        float4 up[VY][R], dn[VY][R];
+#pragma unroll
+        for (int y = 0; y < VY; ++y)
+#pragma unroll
+            for (int j = 1; j <= R; ++j) {
+                if (y - j < 0) up[y][j - 1] = lds4(rows + (my_row + y - j + shift) * LX + lane * 4);
+                if (y + j >= VY) dn[y][j - 1] = lds4(rows + (my_row + y + j + shift) * LX + lane * 4);
+            }
+        // target t is plane zp - R + t, kept in slot (PH - R + t) mod 2R
+#pragma unroll
+        for (int y = 0; y < VY; ++y)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const float x = v[y][e];
+#pragma unroll
+                for (int t = R + 1; t < 2 * R; ++t) {
+                    float& acc = A[L][pmod(PH - R + t, W2)][y][e];
+                    acc = __fmaf_rn(a.cf[cidx<R>(0, -1, t - R)], x, acc);
+                }
+                {
+                    float& acc = A[L][pmod(PH, W2)][y][e];
+                    float s = __fmaf_rn(a.cf[0], x, acc);
+#pragma unroll
+                    for (int j = 1; j <= R; ++j) {
+                        float ym = (y - j >= 0) ? v[y - j][e] : f4get(up[y][j - 1], e);
+                        float yp = (y + j < VY) ? v[y + j][e] : f4get(dn[y][j - 1], e);
+                        s = __fmaf_rn(a.cf[cidx<R>(1, -1, j)], ym, s);
+                        s = __fmaf_rn(a.cf[cidx<R>(1, +1, j)], yp, s);
+                    }
+#pragma unroll
+                    for (int j = 1; j <= R; ++j) {
+                        float xm = (e - j >= 0) ? v[y][e - j] : lft[y][4 + e - j];
+                        float xp = (e + j < 4) ? v[y][e + j] : rgt[y][e + j - 4];
+                        s = __fmaf_rn(a.cf[cidx<R>(2, -1, j)], xm, s);
+                        s = __fmaf_rn(a.cf[cidx<R>(2, +1, j)], xp, s);
+                    }
+                    acc = s;
+                }
+#pragma unroll
+                for (int t = 0; t < R; ++t) {
+                    float& acc = A[L][pmod(PH - R + t, W2)][y][e];
+                    acc = __fmaf_rn(a.cf[cidx<R>(0, +1, R - t)], x, acc);
+                }
+                float& a0 = A[L][pmod(PH - R, W2)][y][e];
+                done[y][e] = a0;
+                a0 = a.cf[cidx<R>(0, -1, R)] * x;  // first contribution to target zp + R
+            }
+    }
+
+    // boundary cells (and whole boundary planes) keep their input value
+    __device__ __forceinline__ void fixup(float (&done)[VY][4], int zt) {
+        const bool zbnd = zt < R || zt >= n0 - R;
+        if (!(zbnd || warp_bnd)) return;
+        if (zt < a.in_lo || zt >= a.in_hi) return;
+        const int64_t slot = (a.in_slot0 + (zt - a.in_lo)) % a.in_cap;
+        const T* base = in + slot * plane;
+#pragma unroll
+        for (int y = 0; y < VY; ++y)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const bool cin = (inyx >> (y * 4 + e)) & 1u;
+                int gy = ys + my_row + y, gx = gx0 + e;
+                if ((zbnd || !cin) && gy >= 0 && gy < ny && gx >= 0 && gx < nx)
+                    done[y][e] = ld1(base + (int64_t)gy * nx + gx);
+            }
+    }
+
+    __device__ __forceinline__ void emit(const float (&done)[VY][4], int zt) {
+        if (zt < olo || zt >= ohi) return;
+        const int lx0 = lane * 4;
+        if (!(lx0 >= S::HXA && lx0 < S::HXA + S::TX && xin)) return;
+        T* ob = out + (int64_t)(zt - (int)a.out_lo) * plane;
 #pragma unroll
         for (int y = 0; y < VY; ++y) {
-            float4 q = lds4(sbuf + (my_row + y + R) * LX + lane * 4);
-            v[y][0] = q.x; v[y][1] = q.y; v[y][2] = q.z; v[y][3] = q.w;
-        }
-        level_arrival<R, VY, T>(A[0], v, sbuf, R, 0, INROWS, my_row, lane, c, inyx, zin, n0, done);
-        // ---- levels 2..K: arrival of the previous level's completed plane
-#pragma unroll
-        for (int l = 1; l < K; ++l) {
-            float* lb = slev + ((l - 1) * 2 + buf) * LYT * LX;
-#pragma unroll
-            for (int y = 0; y < VY; ++y)
-                *reinterpret_cast<float4*>(lb + (my_row + y) * LX + lane * 4) =
-                    make_float4(done[y][0], done[y][1], done[y][2], done[y][3]);
-            __syncthreads();
-#pragma unroll
-            for (int y = 0; y < VY; ++y)
-#pragma unroll
-                for (int e = 0; e < 4; ++e) v[y][e] = done[y][e];
-            level_arrival<R, VY, float>(A[l], v, lb, 0, 0, LYT, my_row, lane, c, inyx, zin - (int64_t)l * R, n0, done);
-        }
-        // ---- store the last level's completed plane
-        const int64_t zo = zin - (int64_t)K * R;
-        if (zo >= a.out_lo && zo < a.out_hi) {
-            const int lx0 = lane * 4;
-            if (lx0 >= S::HXA && lx0 < S::HXA + S::TX && xin) {
-                T* ob = out + (zo - a.out_lo) * plane;
-#pragma unroll
-                for (int y = 0; y < VY; ++y) {
-                    int ty = my_row + y;
-                    int64_t gy = ys + ty;
-                    if (ty >= S::HY && ty < S::HY + S::TY && gy < ny)
-                        st4(ob + gy * nx + gx0, make_float4(done[y][0], done[y][1], done[y][2], done[y][3]));
-                }
-            }
+            int ty = my_row + y;
+            int gy = ys + ty;
+            if (ty >= S::HY && ty < S::HY + S::TY && gy < ny)
+                st4(ob + (int64_t)gy * nx + gx0, make_float4(done[y][0], done[y][1], done[y][2], done[y][3]));
         }
     }
+
+    // level L of phase p (phase PH = p mod 2R): consumes input plane za + p
+    // (L = 0) or what level L-1 completed in phase p-1 (plane za + p - L(R+1))
+    template <int L, int PH>
+    __device__ __forceinline__ void level(int p, const T* sbuf, int buf) {
+        // arrivals that can reach the requested output planes (uniform per CTA)
+        const int zp = za + p - L * (R + 1);
+        const int lo = need_lo - (K - L) * R, hi = need_hi + (K - L) * R;
+        if (zp < za || zp < lo || zp >= hi) {
+            if constexpr (L + 1 < K) level<L + 1, PH>(p, sbuf, buf);
+            return;
+        }
+        float v[VY][4], done[VY][4];
+        if constexpr (L == 0) {
+#pragma unroll
+            for (int y = 0; y < VY; ++y) {
+                float4 q = lds4(sbuf + (my_row + y + R) * LX + lane * 4);
+                v[y][0] = q.x; v[y][1] = q.y; v[y][2] = q.z; v[y][3] = q.w;
+            }
+            arrive<0, PH>(v, sbuf, R, done);
+        } else {
+            const float* prev = slev + ((L - 1) * 2 + (buf ^ 1)) * LROWS * LX;
+#pragma unroll
+            for (int y = 0; y < VY; ++y) {
+                float4 q = lds4(prev + (my_row + y + R) * LX + lane * 4);
+                v[y][0] = q.x; v[y][1] = q.y; v[y][2] = q.z; v[y][3] = q.w;
+            }
+            arrive<L, pmod(PH - L * (R + 1), W2)>(v, prev, R, done);
+        }
+        const int zt = za + p - L * (R + 1) - R;
+        fixup(done, zt);
+        if constexpr (L == K - 1) {
+            emit(done, zt);
+        } else {
+            float* lb = slev + (L * 2 + buf) * LROWS * LX;
+#pragma unroll
+            for (int y = 0; y < VY; ++y)
+                *reinterpret_cast<float4*>(lb + (my_row + y + R) * LX + lane * 4) =
+                    make_float4(done[y][0], done[y][1], done[y][2], done[y][3]);
+        }
+        if constexpr (L + 1 < K) level<L + 1, PH>(p, sbuf, buf);
+    }
+
+    template <int PH>
+    __device__ __forceinline__ void phase(int p0) {
+        const int p = p0 + PH;
+        cp_async_wait_all();
+        __syncthreads();
+        const int buf = PH & 1;  // 2R is even, so p and PH have the same parity
+        stage_plane(za + p + 1, buf ^ 1);
+        level<0, PH>(p, sin + buf * INROWS * LX, buf);
+        if constexpr (PH + 1 < W2) phase<PH + 1>(p0);
+    }
+
+    __device__ __forceinline__ void run(void* smem) {
+        sin = reinterpret_cast<T*>(smem);
+        slev = reinterpret_cast<float*>(smem) + (2 * INROWS * LX * sizeof(T)) / 4;
+        lane = threadIdx.x & 31;
+        warp = threadIdx.x >> 5;
+        my_row = warp * VY;
+        const int x0 = (int)blockIdx.x * S::TX, y0 = (int)blockIdx.y * S::TY;
+        xs = x0 - S::HXA;
+        ys = y0 - S::HY;
+        ny = (int)a.ny;
+        nx = (int)a.nx;
+        plane = a.ny * a.nx;
+        n0 = (int)a.n0;
+        gx0 = xs + lane * 4;
+        xin = gx0 >= 0 && gx0 < nx;  // nx % 4 == 0: a vector is all in or all out
+        in = static_cast<const T*>(a.in);
+        out = static_cast<T*>(a.out);
+        inyx = 0;
+#pragma unroll
+        for (int y = 0; y < VY; ++y)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                int gy = ys + my_row + y, gx = gx0 + e;
+                if (gy >= R && gy < ny - R && gx >= R && gx < nx - R) inyx |= 1u << (y * 4 + e);
+            }
+        warp_bnd = __any_sync(0xffffffffu, inyx != (1u << (4 * VY)) - 1u);
+        rowok = 0;
+#pragma unroll
+        for (int i = 0; i < RPW; ++i) {
+            int gy = ys - R + warp + i * NW;
+            rowoff[i] = gy * nx + gx0;
+            if (xin && gy >= 0 && gy < ny) rowok |= 1u << i;
+        }
+#pragma unroll
+        for (int l = 0; l < K; ++l)
+#pragma unroll
+            for (int q = 0; q < W2; ++q)
+#pragma unroll
+                for (int y = 0; y < VY; ++y)
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) A[l][q][y][e] = 0.f;
+        // axis-0 segment of this CTA: outputs [zs, ze), stream over [za, zb)
+        const int nseg = gridDim.z;
+        const int nout = (int)(a.out_hi - a.out_lo), in_lo = (int)a.in_lo, in_hi = (int)a.in_hi;
+        const int zs = (int)a.out_lo + (int)((int64_t)nout * blockIdx.z / nseg);
+        const int ze = (int)a.out_lo + (int)((int64_t)nout * (blockIdx.z + 1) / nseg);
+        za = zs - K * R > in_lo ? zs - K * R : in_lo;
+        zb = ze + K * R < in_hi ? ze + K * R : in_hi;
+        olo = zs;
+        ohi = ze;
+        slot_next = (int)((a.in_slot0 + (za - in_lo)) % a.in_cap);
+        need_lo = zs > (int)a.out_lo ? zs : (int)a.out_lo;
+        need_hi = ze < (int)a.out_hi ? ze : (int)a.out_hi;
+        // last arrival any level needs: level K-1 at plane need_hi + R - 1
+        const int nph0 = (need_hi + R - 1 - za) + (K - 1) * (R + 1) + 1;
+        const int nph = (nph0 + W2 - 1) / W2 * W2;
+        stage_plane(za, 0);
+        for (int p0 = 0; p0 < nph; p0 += W2) phase<0>(p0);
+        cp_async_wait_all();
+    }
+};
+
+template <typename T, int R, int K>
+__global__ void __launch_bounds__(FastShape<R, K>::NW * 32, 1) star3d_fast_kernel(const StencilArgs a) {
+    extern __shared__ float4 smem4[];
+    FastTB<T, R, K> k(a);
+    k.run(smem4);
 }
 
 }  // namespace so2dr

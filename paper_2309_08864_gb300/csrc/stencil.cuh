@@ -42,6 +42,7 @@ struct StencilArgs {
     int tx, ty;           // output tile
     int* status;          // device status word (index checks)
     double c[kMaxCoeffsDev];
+    float cf[kMaxCoeffsDev];  // the same weights rounded once to FP32
 };
 
 template <typename T> struct Compute { using type = float; };

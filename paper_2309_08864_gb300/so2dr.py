@@ -59,7 +59,7 @@ class OpRec(ctypes.Structure):
                 ("edge_hi", ctypes.c_int), ("src_buf", ctypes.c_int), ("dst_buf", ctypes.c_int),
                 ("src_lo", ctypes.c_int64), ("src_hi", ctypes.c_int64), ("src_slot0", ctypes.c_int64),
                 ("dst_lo", ctypes.c_int64), ("dst_hi", ctypes.c_int64), ("dst_slot0", ctypes.c_int64),
-                ("wait_op", ctypes.c_int64 * 3)]
+                ("wait_op", ctypes.c_int64 * 4)]
 
 
 class BufRec(ctypes.Structure):
@@ -210,7 +210,7 @@ class Plan:
 
     # ------------------------------------------------------------ execution
     def bind(self, in_core=False, arena=None, streams=None):
-        """Lends a torch device arena and three torch streams to the plan."""
+        """Lends a torch device arena and four torch streams to the plan."""
         import torch
         info = self.info
         need = info["arena_bytes_in_core"] if in_core else info["arena_bytes"]
@@ -218,10 +218,10 @@ class Plan:
         if arena is None:
             arena = torch.empty(max(need, 256), dtype=torch.uint8, device="cuda")
         if streams is None:
-            streams = [torch.cuda.Stream() for _ in range(3)]
-        hs = (ctypes.c_void_p * 3)(*[ctypes.c_void_p(s.cuda_stream) for s in streams])
+            streams = [torch.cuda.Stream() for _ in range(4)]
+        hs = (ctypes.c_void_p * len(streams))(*[ctypes.c_void_p(s.cuda_stream) for s in streams])
         _check(load_library().so2dr_bind(self._h, ctypes.c_void_p(arena.data_ptr()),
-                                         arena.numel() * arena.element_size(), hs, 3))
+                                         arena.numel() * arena.element_size(), hs, len(streams)))
         self._arena = arena
         self._streams = streams
         self._bound_in_core = bool(in_core)

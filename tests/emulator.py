@@ -70,17 +70,18 @@ def replay(plan, u0, coeff_fields=None, in_core=False, seed=0, policy="random"):
             dev[db][slots(o["dst_slot0"], o["dst_hi"] - o["dst_lo"], bufs[db][1])] = out
 
     # per-stream queues
-    queues = [[j for j, o in enumerate(ops) if o["stream"] == s] for s in range(3)]
-    pos = [0, 0, 0]
+    ns = 4
+    queues = [[j for j, o in enumerate(ops) if o["stream"] == s] for s in range(ns)]
+    pos = [0] * ns
     done = np.zeros(len(ops), dtype=bool)
     n_done = 0
     while n_done < len(ops):
         ready = []
-        for s in range(3):
+        for s in range(ns):
             if pos[s] < len(queues[s]):
                 j = queues[s][pos[s]]
                 w = ops[j]["wait_op"]
-                if all(w[t] < 0 or done[w[t]] for t in range(3)):
+                if all(w[t] < 0 or done[w[t]] for t in range(ns)):
                     ready.append(s)
         assert ready, "deadlock in the op list"
         if policy == "random":

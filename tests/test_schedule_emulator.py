@@ -73,6 +73,7 @@ def test_emulator_detects_a_missing_wait():
             w = list(o["wait_op"])
             w[0] = -1
             o["wait_op"] = tuple(w)
+    assert any(o["kind"] == 1 and o["wait_op"][0] >= 0 for o in ops)
     p.ops = lambda in_core=False: broken if not in_core else ops
     u0 = inputs.draw_box(1, dims)
     ref = oracle.run(u0, c, r, 0, T)
