@@ -263,6 +263,36 @@ int so2dr_loss(so2dr_plan_t plan, const void* host_u0, const void* host_coeff_fi
 int so2dr_dot(so2dr_plan_t plan, const void* host_a, const void* host_b, int64_t n, int dtype,
               double* out);
 
+/*
+ * Allocation-free in-core run (the paper has no counterpart: this entry point
+ * exists for callers that cannot allocate memory -- code running while a CUDA
+ * graph is captured, real-time loops that forbid allocation after start-up,
+ * host runtimes that only hand out pre-registered device buffers).
+ *
+ * Runs `steps` time steps of a constant-coefficient star stencil (2D or 3D)
+ * or 2D box stencil, of the given radius, coefficient table (see so2dr_kind)
+ * and storage dtype, on a grid that is already on the device: d_in is read,
+ * d_out receives the result (distinct, caller-owned device buffers of
+ * dims[0]*dims[1](*dims[2]) elements; d_in is not modified).  Launch depths
+ * follow Algorithm 1: floor(steps/k_on) k_on-step launches, then the
+ * residual, on `stream` (a cudaStream_t; NULL = the legacy default stream).
+ * The call returns once the launches are queued; it does not synchronise.
+ *
+ * It calls no cudaMalloc, cudaFree or other allocating routine, on the device
+ * or the host.  Its one scratch grid lives in a file-scope device array of
+ * 32 MiB that every GPU loading the library holds until the process exits:
+ * grids above 32 MiB are rejected with SO2DR_E_INFEASIBLE.  The first call
+ * on each device looks up that array's device address (cudaGetSymbolAddress
+ * with the device current), so make that first call before any stream
+ * capture.  Every call shares the array and leaves the last call's data in
+ * it (nothing in it has to start at zero: each launch overwrites every cell
+ * it later reads); calls whose work overlaps on the GPU race on it, so
+ * serialise them (one stream, or events).
+ */
+int so2dr_run_device_noalloc(int ndim, const int64_t* dims, int radius, int kind, const double* coeffs,
+                             int ncoeffs, int64_t steps, int k_on, int dtype, const void* d_in, void* d_out,
+                             void* stream);
+
 void so2dr_destroy(so2dr_plan_t plan);
 
 const char* so2dr_strerror(int status);

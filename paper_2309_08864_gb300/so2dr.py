@@ -22,7 +22,8 @@ OK, E_INVAL, E_INFEASIBLE, E_NOT_BOUND, E_CUDA, E_TIMEOUT, E_DEVICE_CHECK, E_NOM
 
 SYMBOLS = ["so2dr_plan", "so2dr_plan_ex", "so2dr_plan_info", "so2dr_plan_chunks", "so2dr_plan_ops",
            "so2dr_plan_buffers", "so2dr_bind", "so2dr_run", "so2dr_adjoint", "so2dr_loss", "so2dr_dot",
-           "so2dr_destroy", "so2dr_strerror", "so2dr_last_error", "so2dr_abi_version"]
+           "so2dr_destroy", "so2dr_strerror", "so2dr_last_error", "so2dr_abi_version",
+           "so2dr_run_device_noalloc"]
 
 
 class So2drError(RuntimeError):
@@ -98,6 +99,7 @@ def load_library(path=None):
     lib.so2dr_adjoint.argtypes = [vp, vp, vp, vp, vp, vp, vp, c_size, c_int, dp, ctypes.POINTER(Stats)]
     lib.so2dr_loss.argtypes = [vp, vp, vp, vp, vp, c_size, dp]
     lib.so2dr_dot.argtypes = [vp, vp, vp, i64, c_int, dp]
+    lib.so2dr_run_device_noalloc.argtypes = [c_int, i64p, c_int, c_int, dp, c_int, i64, c_int, c_int, vp, vp, vp]
     lib.so2dr_destroy.argtypes = [vp]
     lib.so2dr_destroy.restype = None
     lib.so2dr_strerror.argtypes = [c_int]
