@@ -7,11 +7,6 @@
 
 namespace so2dr {
 
-namespace {
-constexpr int64_t kAlign = 256;
-int64_t align_up(int64_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
-int64_t floor_mod(int64_t a, int64_t m) { return ((a % m) + m) % m; }
-}  // namespace
 
 int64_t elem_size(int dtype) {
     switch (dtype) {
@@ -97,77 +92,6 @@ void Tracker::commit(int64_t op, int stream, int64_t wait_op[kNumStreams]) {
     pend_.clear();
 }
 
-// ------------------------------------------------------------- op helpers
-
-namespace {
-
-// Physical slot ranges of grid planes [lo, hi) stored from slot0 in a buffer
-// of capacity cap (split at the wrap).
-void add_buf_access(Tracker& tr, int res, int64_t lo, int64_t hi, int64_t slot0, int64_t cap,
-                    bool write) {
-    int64_t n = hi - lo;
-    if (n <= 0) return;
-    int64_t s0 = floor_mod(slot0, cap);
-    int64_t first = std::min(n, cap - s0);
-    tr.access(res, s0, s0 + first, write);
-    if (n > first) tr.access(res, 0, n - first, write);
-}
-
-struct Emitter {
-    RunList& rl;
-    Tracker tr;
-    // resource ids: 0 = host array(s) (each host array gets its own id below)
-    int host_res_base;
-    Emitter(RunList& r, int nres, int host_base) : rl(r), tr(nres), host_res_base(host_base) {}
-
-    int64_t emit(Op& op) {
-        int64_t idx = (int64_t)rl.ops.size();
-        tr.commit(idx, op.pub.stream, op.pub.wait_op);
-        for (int s = 0; s < kNumStreams; ++s)
-            if (op.pub.wait_op[s] >= 0) rl.ops[op.pub.wait_op[s]].waited = true;
-        rl.ops.push_back(op);
-        return idx;
-    }
-    int buf_res(int buf) const { return buf; }           // device buffers: ids 0..nbuf-1
-    int host_res(int arr) const { return host_res_base + arr; }
-};
-
-Op make_op(int kind, int stream, int round, int chunk) {
-    Op op;
-    so2dr_op_t& p = op.pub;
-    p.kind = kind;
-    p.stream = stream;
-    p.round = round;
-    p.chunk = chunk;
-    p.depth = 0;
-    p.edge_lo = p.edge_hi = 0;
-    p.src_buf = p.dst_buf = kHost;
-    p.src_lo = p.src_hi = p.src_slot0 = 0;
-    p.dst_lo = p.dst_hi = p.dst_slot0 = 0;
-    for (int s = 0; s < kNumStreams; ++s) p.wait_op[s] = -1;
-    return op;
-}
-
-struct ChunkGeom {
-    int64_t s, e;      // owned planes
-    int64_t a, b;      // input planes of the round
-    int64_t lo, hi;    // new planes sent this round
-};
-
-ChunkGeom chunk_geom(const Plan& p, int i, int kk) {
-    ChunkGeom g;
-    g.s = p.starts[i];
-    g.e = p.starts[i + 1];
-    int64_t h = (int64_t)p.r * kk;
-    g.a = std::max<int64_t>(0, g.s - h);
-    g.b = std::min<int64_t>(p.n0, g.e + h);
-    g.lo = (i == 0) ? 0 : std::min<int64_t>(p.n0, g.s + h);
-    g.hi = (i == p.d - 1) ? p.n0 : std::min<int64_t>(p.n0, g.e + h);
-    return g;
-}
-
-}  // namespace
-
 // Buffer ids of the out-of-core forward list.
 enum { kBufIn = 0, kBufCoef = 1, kBufX = 2, kBufY = 3, kBufOut0 = 4 };
 constexpr int kNumOut = 2;
@@ -221,15 +145,26 @@ static size_t forward_arena(const Plan& p, std::vector<Buffer>* out) {
     return (size_t)off;
 }
 
+size_t forward_arena_bytes(const Plan& p) { return forward_arena(p, nullptr); }
+
 bool build_forward_ooc(const Plan& p, RunList& rl, size_t budget) {
+    return build_forward_ooc_ex(p, rl, budget, ForwardOpts());
+}
+
+bool build_forward_ooc_ex(const Plan& p, RunList& rl, size_t budget, const ForwardOpts& opt) {
     rl.ops.clear();
     size_t need = forward_arena(p, &rl.bufs);
     rl.arena_bytes = need;
     if (budget && need > budget) return false;
     const int nbuf = (int)rl.bufs.size();
     const bool vc = p.kind == SO2DR_VARCOEF_STAR;
-    // host arrays: 0 = grid, 1 = coefficient fields
-    Emitter em(rl, nbuf + 2, nbuf);
+    auto src_of = [&](int t) { return t < (int)opt.src_array.size() ? opt.src_array[t] : 0; };
+    auto dst_of = [&](int t) { return t < (int)opt.dst_array.size() ? opt.dst_array[t] : 0; };
+    int nhost = opt.coef_array + 1;
+    for (int v : opt.src_array) nhost = std::max(nhost, v + 1);
+    for (int v : opt.dst_array) nhost = std::max(nhost, v + 1);
+    // host arrays: the grid's source/destination per round, the face fields
+    Emitter em(rl, nbuf + nhost, nbuf);
     const int64_t cin = rl.bufs[kBufIn].cap;
     int64_t g = 0;
     for (int t = 0; t < p.rounds; ++t) {
@@ -243,7 +178,7 @@ bool build_forward_ooc(const Plan& p, RunList& rl, size_t budget) {
                 for (int f = 0; f < (vc ? 2 : 1); ++f) {
                     int buf = f ? kBufCoef : kBufIn;
                     Op op = make_op(kOpH2D, kStreamH2D, t, i);
-                    op.host_array = f;
+                    op.host_array = f ? opt.coef_array : src_of(t);
                     op.nfields = f ? 6 : 1;
                     op.field_elems = p.n0 * p.plane_cells;
                     op.pub.src_buf = kHost;
@@ -254,7 +189,7 @@ bool build_forward_ooc(const Plan& p, RunList& rl, size_t budget) {
                     op.pub.dst_lo = cg.lo;
                     op.pub.dst_hi = cg.hi;
                     op.pub.dst_slot0 = floor_mod(V + cg.lo, cin);
-                    em.tr.access(em.host_res(f), cg.lo, cg.hi, false);
+                    em.tr.access(em.host_res(op.host_array), cg.lo, cg.hi, false);
                     add_buf_access(em.tr, buf, cg.lo, cg.hi, op.pub.dst_slot0, cin, true);
                     em.emit(op);
                 }
@@ -306,10 +241,11 @@ bool build_forward_ooc(const Plan& p, RunList& rl, size_t budget) {
                 src_slot0 = 0;
             }
             // (Algorithm 1) transfer the chunk back: its owned interior planes
-            int64_t dlo = std::max<int64_t>(cg.s, p.r), dhi = std::min<int64_t>(cg.e, p.n0 - p.r);
+            int64_t dlo = opt.all_planes ? cg.s : std::max<int64_t>(cg.s, p.r);
+            int64_t dhi = opt.all_planes ? cg.e : std::min<int64_t>(cg.e, p.n0 - p.r);
             if (dhi > dlo) {
                 Op op = make_op(kOpD2H, kStreamD2H, t, i);
-                op.host_array = 0;
+                op.host_array = dst_of(t);
                 op.pub.src_buf = src;
                 op.pub.src_lo = dlo;
                 op.pub.src_hi = dhi;
@@ -319,7 +255,7 @@ bool build_forward_ooc(const Plan& p, RunList& rl, size_t budget) {
                 op.pub.dst_hi = dhi;
                 op.pub.dst_slot0 = dlo;
                 add_buf_access(em.tr, src, dlo, dhi, dlo - cg.s, rl.bufs[src].cap, false);
-                em.tr.access(em.host_res(0), dlo, dhi, true);
+                em.tr.access(em.host_res(op.host_array), dlo, dhi, true);
                 em.emit(op);
             }
         }
@@ -463,7 +399,7 @@ double predict_ms(const Plan& p) {
 
 // ------------------------------------------------------------- build_plan
 
-static void partition(Plan& p) {
+void partition_planes(Plan& p) {
     int64_t M = p.n0 - 2 * p.r;
     p.starts.assign(p.d + 1, 0);
     for (int i = 1; i < p.d; ++i) p.starts[i] = p.r + (M * i) / p.d;
@@ -480,7 +416,7 @@ static int fit_chunks(Plan& p, int dmin) {
     if (lo > dmax) return 0;
     auto fits = [&](int d) {
         p.d = d;
-        partition(p);
+        partition_planes(p);
         return !p.budget || forward_arena(p, nullptr) <= p.budget;
     };
     if (!fits(dmax)) return 0;
@@ -491,7 +427,7 @@ static int fit_chunks(Plan& p, int dmin) {
         if (fits(m)) b = m; else a = m;
     }
     p.d = b;
-    partition(p);
+    partition_planes(p);
     return b;
 }
 
@@ -547,13 +483,13 @@ int build_plan(Plan& p, int ndim, const int64_t* dims, int radius, int kind, con
         p.k_on = std::max(1, k_on);
         p.rounds = 0;
         p.d = 1;
-        partition(p);
+        partition_planes(p);
     } else if (T == 0) {
         p.k_off = std::max(1, k_off);
         p.k_on = std::max(1, std::min(k_on ? k_on : 1, p.k_off));
         p.rounds = 0;
         p.d = std::min<int64_t>(min_chunks, p.n0 - 2 * p.r);
-        partition(p);
+        partition_planes(p);
     } else {
         std::vector<int> kons, koffs;
         if (k_on) kons.push_back(k_on);
@@ -587,10 +523,18 @@ int build_plan(Plan& p, int ndim, const int64_t* dims, int radius, int kind, con
         p.k_on = bkn;
         p.rounds = (int)((T + bko - 1) / bko);
         p.d = bd;
-        partition(p);
+        partition_planes(p);
     }
     if (!build_forward_ooc(p, p.ooc, p.budget))
         return fail(SO2DR_E_INFEASIBLE, "no chunking fits the device budget");
+    if (p.kind == SO2DR_VARCOEF_STAR && p.budget && p.n0 - 2 * p.r >= 1) {
+        // the adjoint's single-step rounds must fit as well (at the most chunks)
+        Plan q = p;
+        q.d = (int)std::max<int64_t>(1, p.n0 - 2 * p.r);
+        partition_planes(q);
+        if (adjoint_arena_bytes(q) > p.budget)
+            return fail(SO2DR_E_INFEASIBLE, "the adjoint rounds do not fit the device budget");
+    }
     build_forward_in_core(p, p.ic);
     int64_t cin, cx, cy, co;
     forward_caps(p, &cin, &cx, &cy, &co);

@@ -46,6 +46,8 @@ struct Op {
     int64_t aux_lo = 0, aux_slot0 = 0;
     int aux2_buf = -1;
     int64_t aux2_lo = 0, aux2_slot0 = 0;
+    int aux3_buf = -1;
+    int64_t aux3_lo = 0, aux3_slot0 = 0;
     int64_t arg0 = 0, arg1 = 0;  // kernel-specific integers
     bool waited = false;    // some later op waits on this op's completion event
 };
@@ -125,9 +127,94 @@ int num_coeffs(int ndim, int radius, int kind);
 bool build_forward_ooc(const Plan& p, RunList& rl, size_t budget);
 void build_forward_in_core(const Plan& p, RunList& rl);
 
-// Adjoint pipeline pieces (built per call; see run.cu).
-struct AdjLayout {
-    RunList fwd_store;   // forward that also writes every level (recompute)
+// Options of a forward op list used inside the adjoint pipeline.
+struct ForwardOpts {
+    std::vector<int> src_array;  // host array each round reads (default: 0, in place)
+    std::vector<int> dst_array;  // host array each round writes (default: 0)
+    bool all_planes = false;     // write back the axis-0 boundary planes too
+    int coef_array = 1;          // host array of the face fields
 };
+
+// Forward op list with per-round source/destination host arrays.
+bool build_forward_ooc_ex(const Plan& p, RunList& rl, size_t budget, const ForwardOpts& opt);
+
+// Arena bytes of the forward op list for the plan's chunking.
+size_t forward_arena_bytes(const Plan& p);
+
+// Splits [0, n0) into d chunks (interior planes spread evenly).
+void partition_planes(Plan& p);
+
+// Arena bytes of the single-step adjoint rounds for q's chunking (adjoint.cu).
+size_t adjoint_arena_bytes(const Plan& q);
+
+// ------------------------------------------------------------- op helpers
+
+constexpr int64_t kAlign = 256;
+inline int64_t align_up(int64_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+inline int64_t floor_mod(int64_t a, int64_t m) { return ((a % m) + m) % m; }
+
+// Physical slot ranges of grid planes [lo, hi) stored from slot0 in a buffer
+// of capacity cap (split at the wrap).
+inline void add_buf_access(Tracker& tr, int res, int64_t lo, int64_t hi, int64_t slot0, int64_t cap,
+                           bool write) {
+    int64_t n = hi - lo;
+    if (n <= 0 || cap <= 0) return;
+    int64_t s0 = floor_mod(slot0, cap);
+    int64_t first = n < cap - s0 ? n : cap - s0;
+    tr.access(res, s0, s0 + first, write);
+    if (n > first) tr.access(res, 0, n - first, write);
+}
+
+// Appends ops to a RunList, computing each op's cross-stream waits.
+// Resources: device buffers 0..nbuf-1, host arrays nbuf..nbuf+nhost-1.
+struct Emitter {
+    RunList& rl;
+    Tracker tr;
+    int host_res_base;
+    Emitter(RunList& r, int nres, int host_base) : rl(r), tr(nres), host_res_base(host_base) {}
+    int64_t emit(Op& op) {
+        int64_t idx = (int64_t)rl.ops.size();
+        tr.commit(idx, op.pub.stream, op.pub.wait_op);
+        for (int s = 0; s < kNumStreams; ++s)
+            if (op.pub.wait_op[s] >= 0) rl.ops[op.pub.wait_op[s]].waited = true;
+        rl.ops.push_back(op);
+        return idx;
+    }
+    int host_res(int arr) const { return host_res_base + arr; }
+};
+
+inline Op make_op(int kind, int stream, int round, int chunk) {
+    Op op;
+    so2dr_op_t& p = op.pub;
+    p.kind = kind;
+    p.stream = stream;
+    p.round = round;
+    p.chunk = chunk;
+    p.depth = 0;
+    p.edge_lo = p.edge_hi = 0;
+    p.src_buf = p.dst_buf = kHost;
+    p.src_lo = p.src_hi = p.src_slot0 = 0;
+    p.dst_lo = p.dst_hi = p.dst_slot0 = 0;
+    for (int s = 0; s < kNumStreams; ++s) p.wait_op[s] = -1;
+    return op;
+}
+
+struct ChunkGeom {
+    int64_t s, e;      // owned planes
+    int64_t a, b;      // input planes of the round
+    int64_t lo, hi;    // new planes sent this round
+};
+
+inline ChunkGeom chunk_geom(const Plan& p, int i, int kk) {
+    ChunkGeom g;
+    g.s = p.starts[i];
+    g.e = p.starts[i + 1];
+    int64_t h = (int64_t)p.r * kk;
+    g.a = g.s - h > 0 ? g.s - h : 0;
+    g.b = g.e + h < p.n0 ? g.e + h : p.n0;
+    g.lo = (i == 0) ? 0 : (g.s + h < p.n0 ? g.s + h : p.n0);
+    g.hi = (i == p.d - 1) ? p.n0 : (g.e + h < p.n0 ? g.e + h : p.n0);
+    return g;
+}
 
 }  // namespace so2dr

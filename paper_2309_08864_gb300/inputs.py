@@ -61,6 +61,8 @@ def draw_box(seed, shape, lo=None, hi=None, dist="uniform", a=0.0, b=1.0,
     'normal' -> mean a, deviation b.  `out` may be a preallocated contiguous
     array (numpy or anything exposing a data pointer via __array_interface__)."""
     nd = len(shape)
+    if nd > 3:
+        raise ValueError("draw_box handles grids of up to 3 dimensions")
     lo = [0] * nd if lo is None else list(lo)
     hi = list(shape) if hi is None else list(hi)
     ext = tuple(h - l for l, h in zip(lo, hi))

@@ -154,6 +154,7 @@ class Plan:
                                float(link_gbs[0]), float(link_gbs[1]), float(hbm_gbs))
         _check(rc)
         self._h = h
+        self._budget = int(budget_bytes)
         self._arena = None
         self._streams = None
         self._bound_in_core = None
@@ -216,7 +217,9 @@ class Plan:
         import torch
         info = self.info
         need = info["arena_bytes_in_core"] if in_core else info["arena_bytes"]
-        need = max(need, info["arena_bytes"])  if not in_core else need
+        if self.kind == VARCOEF_STAR and not in_core and self._budget:
+            # the adjoint's pipelines fit their own chunkings into the bound arena
+            need = max(need, self._budget)
         if arena is None:
             arena = torch.empty(max(need, 256), dtype=torch.uint8, device="cuda")
         if streams is None:
@@ -260,6 +263,15 @@ class Plan:
                                          _ptr(workspace), nbytes, ctypes.byref(loss)))
         return loss.value
 
+    def workspace(self, checkpoint_every=8):
+        """Pinned host workspace so2dr_adjoint needs: (segments + C - 1) grids."""
+        import torch
+        info = self.info
+        T, C = info["time_steps"], int(checkpoint_every)
+        S = max(1, -(-T // C))
+        grid = info["dims"][0] * info["dims"][1] * max(1, info["dims"][2]) * (8 if self.dtype == F64 else 4)
+        return torch.empty((S + C - 1) * grid, dtype=torch.uint8).pin_memory()
+
     def dot(self, a, b):
         if self._arena is None:
             self.bind()
@@ -267,3 +279,41 @@ class Plan:
         dt = F64 if str(a.dtype).endswith("float64") else F32
         _check(load_library().so2dr_dot(self._h, _ptr(a), _ptr(b), int(a.numel()), dt, ctypes.byref(out)))
         return out.value
+
+
+def _varcoef_loss_fn():
+    import torch
+
+    class VarcoefLoss(torch.autograd.Function):
+        """L = 1/2 ||u_T - u*||^2 of the variable-coefficient sweep, with
+        gradients w.r.t. the initial field and the six face fields from the
+        out-of-core adjoint (so2dr_adjoint)."""
+
+        @staticmethod
+        def forward(ctx, u0, faces, target, plan, checkpoint_every):
+            pin = lambda t: t.detach().contiguous() if t.is_pinned() else t.detach().contiguous().pin_memory()
+            u0p, fp, tp = pin(u0), pin(faces), pin(target)
+            gu = torch.empty_like(u0p).pin_memory()
+            gc = torch.empty_like(fp).pin_memory()
+            ws = plan.workspace(checkpoint_every)
+            loss, _ = plan.adjoint(u0p, fp, tp, gu, gc, ws, checkpoint_every, stats=False)
+            ctx.save_for_backward(gu, gc)
+            return torch.tensor(loss, dtype=torch.float64)
+
+        @staticmethod
+        def backward(ctx, g):
+            gu, gc = ctx.saved_tensors
+            return (g * gu).to(gu.dtype), (g * gc).to(gc.dtype), None, None, None
+
+    return VarcoefLoss
+
+
+_VL = None
+
+
+def varcoef_loss(u0, faces, target, plan, checkpoint_every=8):
+    """Differentiable loss through the out-of-core pipeline (torch.autograd)."""
+    global _VL
+    if _VL is None:
+        _VL = _varcoef_loss_fn()
+    return _VL.apply(u0, faces, target, plan, checkpoint_every)

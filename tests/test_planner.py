@@ -130,3 +130,10 @@ def test_auto_parameters_fit_the_budget():
     assert info["arena_bytes"] <= 1 << 30
     assert info["chunks"] >= 8
     assert 1 <= info["k_on"] <= info["k_off"] <= 64
+
+
+def test_varcoef_plan_rejects_budgets_the_adjoint_cannot_fit():
+    with pytest.raises(so2dr.So2drError) as e:
+        so2dr.Plan((16, 12, 16), 1, "varcoef", None, 5, min_chunks=1, k_on=2, k_off=1, budget_bytes=40 << 10,
+                   dtype="f32")
+    assert e.value.code == so2dr.E_INFEASIBLE and "adjoint" in str(e.value)
