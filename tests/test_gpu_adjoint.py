@@ -71,8 +71,10 @@ def fd_check(dims, T, C, budget, n_dirs_u, n_dirs_c, tol, eps_c_rel=1e-3):
     gu_ = torch.empty_like(tu0).pin_memory()
     gc_ = torch.empty_like(tf).pin_memory()
     loss, st = p32.adjoint(tu0, tf, tt, gu_, gc_, p32.workspace(C), C)
+    print("ADJOINT %s T=%d: %.1f ms, %.2f Gcell/s (forward + adjoint updates), chunks %d" % (
+        dims, T, st["total_ms"], st["gcells_per_s"], p32.info["chunks"]))
     # FP64 copies of the same inputs (FP32 values are exact in FP64)
-    p64 = so2dr.Plan(dims, 1, "varcoef", None, T, min_chunks=1, k_on=4, k_off=C, budget_bytes=2 * budget,
+    p64 = so2dr.Plan(dims, 1, "varcoef", None, T, min_chunks=1, k_on=4, k_off=C, budget_bytes=4 * budget,
                      dtype=so2dr.F64)
     u64, f64, t64 = u0.astype(np.float64), faces.astype(np.float64), tgt.astype(np.float64)
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()

@@ -75,3 +75,42 @@ def test_c3_25pt_r4_1536cubed_fp32_full_size():
     c = inputs.radius4_star_coeffs()
     host, starts, info = _full_run(dims, r, c, T, so2dr.F32, 4 << 30, 1, in_core_check=True)
     cone_check(dims, r, c, T, so2dr.F32, host, starts, 1e-5, n_random=1)
+
+
+def test_c4_precision_forms_1024cubed_128_steps():
+    """Storage in FP32 / BF16 / FP16 with FP32 arithmetic, 1 GiB budget: the
+    error against the FP64 oracle (same rounded input) on sampled cones, and
+    out-of-core byte-identical to in-core for the 16-bit forms."""
+    import json
+    import torch
+    dims, r, T = (1024, 1024, 1024), 1, 128
+    coeffs = [0.4] + [0.1] * 6
+    report = {}
+    for dtype, tol, koff in ((so2dr.F32, 1e-5, 8), (so2dr.BF16, 3e-2, 16), (so2dr.F16, 5e-3, 16)):
+        host, starts, info = _full_run(dims, r, coeffs, T, dtype, 1 << 30, 8, k_on=4, k_off=koff,
+                                       in_core_check=(dtype == so2dr.BF16))
+        rng = np.random.default_rng(0)
+        errs, l2n, l2d = [], 0.0, 0.0
+        for lo, hi in sample_boxes(dims, starts, rng, n_random=0, w=2)[:3]:
+            blo, bhi = oracle.cone_box(dims, lo, hi, r * T)
+            u32 = inputs.draw_box(1, dims, blo, bhi, as_f32=True)
+            ub = inputs.storage_to_f64(inputs.to_storage(u32.astype(np.float64), dtype), dtype)
+            ref = oracle.run_cone(ub, gu.compute_coeffs(coeffs, dtype), r, oracle.STAR, T, blo, bhi, dims, lo, hi)
+            got = gu.storage_of(host[tuple(slice(l, h) for l, h in zip(lo, hi))].contiguous(), dtype)
+            errs.append(float(np.max(np.abs(got - ref)) / np.max(np.abs(ref))))
+            l2n += float(np.sum((got - ref) ** 2))
+            l2d += float(np.sum(ref ** 2))
+        report[{so2dr.F32: "f32", so2dr.BF16: "bf16", so2dr.F16: "f16"}[dtype]] = {
+            "rel_linf": max(errs), "rel_l2": (l2n / l2d) ** 0.5, "k_off": info["k_off"], "chunks": info["chunks"]}
+        assert max(errs) <= tol, (dtype, errs)
+        del host
+    print("PRECISION_REPORT " + json.dumps(report))
+
+
+def test_c5_adjoint_512cubed_finite_differences():
+    """Differentiation form at full size: 512^3 FP32, 64 steps, checkpoints
+    every 8 steps, 256 MiB budget; 16 central-difference directions (8 in u0,
+    8 in the face fields) of the FP64 loss against the adjoint gradient."""
+    from tests.test_gpu_adjoint import fd_check
+    err = fd_check((512, 512, 512), 64, 8, 256 << 20, 8, 8, 1e-4)
+    print("C5_FD_MAX_REL_ERR %.3e" % err)
