@@ -32,6 +32,12 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 MEASURED = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# DRAM bytes per algorithmic byte of star3d_fast_kernel<float, 1, 4>, from the
+# full ncu capture of a 512^3 in-core launch (dram__bytes_read.sum +
+# dram__bytes_write.sum = 1123.9 MB for 1073.7 MB of algorithmic reads and
+# writes); traffic grows with the planes a launch streams, so a launch's
+# traffic is this ratio times its (input + output) plane bytes.
+DRAM_PER_ALG_BYTE_R1K4_F32 = 1123.9 / 1073.7
 # host-link bandwidths measured on the GB300 machines with pinned buffers
 # (cudaMemcpyAsync, 4 GiB): host-to-device 211, device-to-host 193, both
 # directions at once 343 GB/s in total.
@@ -56,7 +62,11 @@ CONFIGS = {
                    budget=1 << 30, min_chunks=8, k_on=4, k_off=16),
     "c4-f32": dict(workload="3D 7-point star FP32 storage 1024^3, 128 steps, 1 GiB budget",
                    dims=(1024, 1024, 1024), r=1, coeffs="star7", T=128, dtype="f32",
-                   budget=1 << 30, min_chunks=8, k_on=4, k_off=8),
+                   budget=1 << 30, min_chunks=8, k_on=4, k_off=12),
+    "c5": dict(workload="3D variable-coefficient 7-point FP32 512^3, 64 steps, adjoint with checkpoints "
+                        "every 8 steps, 256 MiB budget",
+               dims=(512, 512, 512), r=1, coeffs=None, T=64, dtype="f32", budget=256 << 20,
+               min_chunks=1, k_on=4, k_off=8, adjoint=True),
 }
 
 
@@ -266,6 +276,62 @@ def run_kernel_case(args):
     return 0
 
 
+def run_adjoint(args, cfg, world, rank, local):
+    """Differentiation form: one step = one so2dr_adjoint (checkpointed forward,
+    loss, recomputation and the transposed stencil backward) over the grid."""
+    import numpy as np
+    import torch
+    from paper_2309_08864_gb300 import inputs, so2dr
+    dims, T, C = cfg["dims"], cfg["T"], cfg["k_off"]
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+    u0 = pin(inputs.draw_box(1, dims, as_f32=True))
+    faces = np.empty((6,) + dims, dtype=np.float32)
+    for f in range(6):
+        inputs.draw_box(100 + f, dims, a=0.05, b=0.15, as_f32=True, out=faces[f])
+    faces = pin(faces)
+    tgt = pin(inputs.draw_box(2, dims, as_f32=True))
+    plan = so2dr.Plan(dims, 1, "varcoef", None, T, min_chunks=cfg["min_chunks"], k_on=cfg["k_on"], k_off=C,
+                      budget_bytes=cfg["budget"], dtype="f32")
+    gu_ = torch.empty_like(u0).pin_memory()
+    gc_ = torch.empty_like(faces).pin_memory()
+    ws = plan.workspace(C)
+    for _ in range(args.warmup):
+        plan.adjoint(u0, faces, tgt, gu_, gc_, ws, C)
+    barrier(world)
+    clocks = ClockSampler(local)
+    clocks.start()
+    stats = []
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        loss, st = plan.adjoint(u0, faces, tgt, gu_, gc_, ws, C)
+        stats.append(st)
+    wall = allreduce_max(time.perf_counter() - t0, world)
+    clk = clocks.stop()
+    inner = 1
+    for e in dims:
+        inner *= e - 2
+    cells = 2.0 * inner * T   # forward + adjoint cell updates
+    ms = allreduce_max(sum(s["total_ms"] for s in stats), world)
+    value = world * cells * args.steps / (ms * 1e-3) / 1e9
+    h2d = stats[-1]["h2d_bytes"]
+    d2h = stats[-1]["d2h_bytes"]
+    line = {"metric": "Gcell-updates/s out-of-core on 1 GB300 (forward + adjoint updates)", "value": value,
+            "unit": "Gcell/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic (SplitMix64-seeded)",
+            "config": {"workload": cfg["workload"], "chunks": plan.info["chunks"], "loss": loss},
+            "e2e": {"value": world * cells * args.steps / wall / 1e9, "unit": "Gcell/s",
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": int(sum(s["launches"] for s in stats)), "clocks": clk,
+            "stage_ms_per_step": {"kernel": sum(s["kernel_ms"] for s in stats) / args.steps,
+                                  "h2d": sum(s["h2d_ms"] for s in stats) / args.steps,
+                                  "d2h": sum(s["d2h_ms"] for s in stats) / args.steps}}
+    plan.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -294,6 +360,8 @@ def main():
     torch.cuda.set_device(local)
     if args.kernel_case:
         return run_kernel_case(args)
+    if cfg.get("adjoint"):
+        return run_adjoint(args, cfg, world, rank, local)
 
     hbm_peak, peak_kind = measured_peaks()
     coeffs = coeffs_of(cfg["coeffs"], inputs)
@@ -331,6 +399,13 @@ def main():
     mk_ms = sum(s["main_kernel_ms"] for s in stats)
     mk_n = sum(s["main_kernel_launches"] for s in stats)
     mk_cells = sum(s["main_kernel_cells"] for s in stats)
+    # (input + output) plane bytes of the k_on-deep launches of one run
+    io_bytes = 0.0
+    n_main = 0
+    for o in plan.ops():
+        if o["kind"] == 1 and o["depth"] == info["k_on"]:
+            io_bytes += ((o["src_hi"] - o["src_lo"]) + (o["dst_hi"] - o["dst_lo"])) * info["plane_bytes"]
+            n_main += 1
     b = {"f64": 8, "f32": 4, "bf16": 2, "f16": 2}[cfg["dtype"]]
     alg_bytes_per_launch = 2 * b * mk_cells / max(1, mk_n)
     avg_launch_s = mk_ms / max(1, mk_n) * 1e-3
@@ -366,7 +441,9 @@ def main():
                                                 "d2h": d2h / (stats[-1]["d2h_ms"] * 1e-3) / 1e9,
                                                 "both_during_run": (h2d + d2h) / (stats[-1]["total_ms"] * 1e-3) / 1e9}},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                     "frac": achieved / hbm_peak, "traffic": None,
+                     "frac": achieved / hbm_peak,
+                     "traffic": (DRAM_PER_ALG_BYTE_R1K4_F32 * io_bytes / max(1, n_main)
+                                 if (cfg["r"], info["k_on"], cfg["dtype"]) == (1, 4, "f32") else None),
                      "kernel": "star3d_fast_kernel (k_on-step TB launch)", "peak_kind": peak_kind + " (burst)",
                      "avg_launch_ms": avg_launch_s * 1e3, "launches": mk_n},
         "e2e": {"value": e2e, "unit": "Gcell/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
