@@ -3,7 +3,7 @@
 
 #include <cuda_runtime.h>
 
-#include "../../include/so2dr.h"
+#include "so2dr.h"
 #include "stencil.cuh"
 
 namespace so2dr {

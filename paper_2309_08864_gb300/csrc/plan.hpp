@@ -11,7 +11,7 @@
 #include <string>
 #include <vector>
 
-#include "../../include/so2dr.h"
+#include "so2dr.h"
 
 namespace so2dr {
 

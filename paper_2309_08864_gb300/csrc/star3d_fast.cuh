@@ -56,7 +56,11 @@ template <int R, int K> struct FastShape {
     static constexpr int TY = LYT - 2 * HY;
     static constexpr int INROWS = LYT + 2 * R;
     static constexpr int LROWS = LYT + 2 * R;           // level planes with R spare rows each side
-    template <int ES> static constexpr int smem() { return 2 * INROWS * LX * ES + 2 * (K - 1) * LROWS * LX * 4; }
+    // planes kept per level: the arrival of the current phase, the one being
+    // written, and the R older ones whose values boundary cells take back on
+    // completion
+    static constexpr int NB = R + 2;
+    template <int ES> static constexpr int smem() { return NB * INROWS * LX * ES + NB * (K - 1) * LROWS * LX * 4; }
 };
 
 template <typename T> __device__ __forceinline__ void cp_async_vec4(T* sdst, const T* gsrc, bool valid) {
@@ -117,11 +121,11 @@ template <typename T, int R, int K>
 struct FastTB {
     using S = FastShape<R, K>;
     static constexpr int VY = S::VY, NW = S::NW, LX = S::LX, LYT = S::LYT, INROWS = S::INROWS;
-    static constexpr int RPW = (INROWS + NW - 1) / NW, W2 = 2 * R, NC = 1 + 6 * R, LROWS = S::LROWS;
+    static constexpr int RPW = (INROWS + NW - 1) / NW, W2 = 2 * R, NC = 1 + 6 * R, LROWS = S::LROWS, NB = S::NB;
 
     const StencilArgs& a;
-    T* sin;        // [2][INROWS][LX] staged input planes
-    float* slev;   // [K-1][2][LROWS][LX] completed planes of levels 0..K-2 (R spare rows each side)
+    T* sin;        // [NB][INROWS][LX] staged input planes (plane of phase p in slot p % NB)
+    float* slev;   // [K-1][NB][LROWS][LX] completed planes of levels 0..K-2 (R spare rows each side)
     int rowoff[RPW];   // element offset of each staged row inside a plane
     unsigned rowok;    // bit i: staged row i lies inside the grid
     int lane, warp, my_row, n0, olo, ohi;
@@ -216,22 +220,23 @@ struct FastTB {
             }
     }
 
-    // boundary cells (and whole boundary planes) keep their input value
-    __device__ __forceinline__ void fixup(float (&done)[VY][4], int zt) {
+    // Boundary cells (and whole boundary planes) keep their value: on
+    // completion they take back the value they had at their centre arrival,
+    // R phases ago, still resident in slot `cs` of the arrival planes.
+    template <typename ST>
+    __device__ __forceinline__ void fixup(float (&done)[VY][4], int zt, const ST* cen) {
         const bool zbnd = zt < R || zt >= n0 - R;
         if (!(zbnd || warp_bnd)) return;
-        if (zt < a.in_lo || zt >= a.in_hi) return;
-        const int64_t slot = (a.in_slot0 + (zt - a.in_lo)) % a.in_cap;
-        const T* base = in + slot * plane;
 #pragma unroll
-        for (int y = 0; y < VY; ++y)
+        for (int y = 0; y < VY; ++y) {
+            const unsigned rowmask = (inyx >> (y * 4)) & 0xFu;
+            if (zbnd || rowmask != 0xFu) {
+                float4 q = lds4(cen + (my_row + y + R) * LX + lane * 4);
 #pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const bool cin = (inyx >> (y * 4 + e)) & 1u;
-                int gy = ys + my_row + y, gx = gx0 + e;
-                if ((zbnd || !cin) && gy >= 0 && gy < ny && gx >= 0 && gx < nx)
-                    done[y][e] = ld1(base + (int64_t)gy * nx + gx);
+                for (int e = 0; e < 4; ++e)
+                    if (zbnd || !((rowmask >> e) & 1u)) done[y][e] = f4get(q, e);
             }
+        }
     }
 
     __device__ __forceinline__ void emit(const float (&done)[VY][4], int zt) {
@@ -252,6 +257,8 @@ struct FastTB {
     // (L = 0) or what level L-1 completed in phase p-1 (plane za + p - L(R+1))
     template <int L, int PH>
     __device__ __forceinline__ void level(int p, const T* sbuf, int buf) {
+        // buf = p % NB: the slot this phase writes (and, for level 0, reads);
+        // arrivals from the level below were written in phase p-1
         // arrivals that can reach the requested output planes (uniform per CTA)
         const int zp = za + p - L * (R + 1);
         const int lo = need_lo - (K - L) * R, hi = need_hi + (K - L) * R;
@@ -260,6 +267,7 @@ struct FastTB {
             return;
         }
         float v[VY][4], done[VY][4];
+        const int zt = za + p - L * (R + 1) - R;
         if constexpr (L == 0) {
 #pragma unroll
             for (int y = 0; y < VY; ++y) {
@@ -267,21 +275,22 @@ struct FastTB {
                 v[y][0] = q.x; v[y][1] = q.y; v[y][2] = q.z; v[y][3] = q.w;
             }
             arrive<0, PH>(v, sbuf, R, done);
+            fixup(done, zt, sin + ((p - R + NB * R) % NB) * INROWS * LX);
         } else {
-            const float* prev = slev + ((L - 1) * 2 + (buf ^ 1)) * LROWS * LX;
+            const int pa = (p - 1 + NB) % NB;  // slot written in phase p-1
+            const float* prev = slev + ((L - 1) * NB + pa) * LROWS * LX;
 #pragma unroll
             for (int y = 0; y < VY; ++y) {
                 float4 q = lds4(prev + (my_row + y + R) * LX + lane * 4);
                 v[y][0] = q.x; v[y][1] = q.y; v[y][2] = q.z; v[y][3] = q.w;
             }
             arrive<L, pmod(PH - L * (R + 1), W2)>(v, prev, R, done);
+            fixup(done, zt, slev + ((L - 1) * NB + (p - 1 - R + NB * (R + 1)) % NB) * LROWS * LX);
         }
-        const int zt = za + p - L * (R + 1) - R;
-        fixup(done, zt);
         if constexpr (L == K - 1) {
             emit(done, zt);
         } else {
-            float* lb = slev + (L * 2 + buf) * LROWS * LX;
+            float* lb = slev + (L * NB + buf) * LROWS * LX;
 #pragma unroll
             for (int y = 0; y < VY; ++y)
                 *reinterpret_cast<float4*>(lb + (my_row + y + R) * LX + lane * 4) =
@@ -295,15 +304,15 @@ struct FastTB {
         const int p = p0 + PH;
         cp_async_wait_all();
         __syncthreads();
-        const int buf = PH & 1;  // 2R is even, so p and PH have the same parity
-        stage_plane(za + p + 1, buf ^ 1);
+        const int buf = p % NB;
+        stage_plane(za + p + 1, (p + 1) % NB);
         level<0, PH>(p, sin + buf * INROWS * LX, buf);
         if constexpr (PH + 1 < W2) phase<PH + 1>(p0);
     }
 
     __device__ __forceinline__ void run(void* smem) {
         sin = reinterpret_cast<T*>(smem);
-        slev = reinterpret_cast<float*>(smem) + (2 * INROWS * LX * sizeof(T)) / 4;
+        slev = reinterpret_cast<float*>(smem) + (NB * INROWS * LX * sizeof(T)) / 4;
         lane = threadIdx.x & 31;
         warp = threadIdx.x >> 5;
         my_row = warp * VY;
