@@ -50,7 +50,7 @@ CONFIGS = {
                min_chunks=4, k_on=4, k_off=8, zero_ring=True),
     "c2": dict(workload="3D 7-point star FP32 1024^3 (4 GiB), 64 steps, 1 GiB budget",
                dims=(1024, 1024, 1024), r=1, coeffs="star7", T=64, dtype="f32", budget=1 << 30,
-               min_chunks=8, k_on=4, k_off=12),
+               min_chunks=8, k_on=4, k_off=16),
     "c3": dict(workload="3D 25-point star r=4 FP32 1536^3 (14.5 GB), 32 steps, 4 GiB budget",
                dims=(1536, 1536, 1536), r=4, coeffs="r4", T=32, dtype="f32", budget=4 << 30,
                min_chunks=1, k_on=1, k_off=8),
@@ -431,6 +431,7 @@ def main():
                    "time_steps": cfg["T"], "device_budget_bytes": cfg["budget"], "k_off": info["k_off"],
                    "k_on": info["k_on"], "chunks": info["chunks"], "rounds": R,
                    "ring_planes": info["ring_planes"], "arena_bytes": info["arena_bytes"],
+                   "lookahead": info["lookahead"], "out_slabs": info["out_slabs"],
                    "redundancy": info["redundancy"], "parallelism": "replicas" if world > 1 else "1 GPU",
                    "l2": "inputs larger than L2 (grid of %.1f GiB vs 126 MB L2)" % (Nb / 2 ** 30)},
         "path_roofline": {"bound": "host-link" if b_host / LINK_BIDIR_GBS >= b_hbm / hbm_peak else "hbm",

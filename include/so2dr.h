@@ -106,6 +106,10 @@ typedef struct {
     double d2h_bytes_per_run;
     double cell_updates_per_run; /* interior cells x time steps                    */
     double redundancy;       /* computed / useful cell updates - 1 (trapezoids)     */
+    int lookahead;           /* 1: the circular buffer also holds the next chunk's new
+                                planes, so transfers run a chunk ahead of the kernels */
+    int out_slabs;           /* output slabs (2: a chunk's device-to-host copy overlaps
+                                the next chunk's last launch)                        */
 } so2dr_plan_info_t;
 
 /* Filled by so2dr_run / so2dr_adjoint when the caller passes a non-NULL pointer. */
@@ -298,7 +302,7 @@ void so2dr_destroy(so2dr_plan_t plan);
 const char* so2dr_strerror(int status);
 const char* so2dr_last_error(void);
 
-/* ABI version of this header (bumped on any incompatible change). */
+/* ABI version of this header (bumped on any incompatible change): 2. */
 int so2dr_abi_version(void);
 
 #ifdef __cplusplus

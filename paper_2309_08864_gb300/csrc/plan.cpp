@@ -3,6 +3,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <limits>
 
 namespace so2dr {
@@ -94,7 +95,7 @@ void Tracker::commit(int64_t op, int stream, int64_t wait_op[kNumStreams]) {
 
 // Buffer ids of the out-of-core forward list.
 enum { kBufIn = 0, kBufCoef = 1, kBufX = 2, kBufY = 3, kBufOut0 = 4 };
-constexpr int kNumOut = 2;
+constexpr int kMaxOut = 2;
 
 // Sizes (planes) of the out-of-core forward buffers for the plan's chunking.
 static void forward_caps(const Plan& p, int64_t* cap_in, int64_t* cap_x, int64_t* cap_y,
@@ -112,7 +113,7 @@ static void forward_caps(const Plan& p, int64_t* cap_in, int64_t* cap_x, int64_t
         ChunkGeom g = chunk_geom(p, i, kk);
         int64_t next_hi = (i + 1 < p.d) ? chunk_geom(p, i + 1, kk).hi
                                         : (p.rounds > 1 ? p.n0 + chunk_geom(p, 0, kk).hi : g.b);
-        cin = std::max(cin, std::max(g.b - g.a, next_hi - g.a));
+        cin = std::max(cin, p.lookahead ? std::max(g.b - g.a, next_hi - g.a) : g.b - g.a);
     }
     int L = (int)launch_depths(p.k_off, p.k_on).size();
     *cap_in = std::max<int64_t>(cin, 1);
@@ -126,7 +127,7 @@ static size_t forward_arena(const Plan& p, std::vector<Buffer>* out) {
     forward_caps(p, &cin, &cx, &cy, &co);
     bool vc = p.kind == SO2DR_VARCOEF_STAR;
     int64_t cbytes = (p.dtype == SO2DR_F64) ? 8 : 4;
-    std::vector<Buffer> b(kBufOut0 + kNumOut);
+    std::vector<Buffer> b(kBufOut0 + kMaxOut);
     int64_t off = 0;
     auto place = [&](int id, int64_t cap, int64_t pb, int nf) {
         b[id].offset = off;
@@ -139,7 +140,7 @@ static size_t forward_arena(const Plan& p, std::vector<Buffer>* out) {
     place(kBufCoef, vc ? cin : 0, 6 * p.plane_cells * cbytes, 6);
     place(kBufX, cx, p.plane_bytes, 1);
     place(kBufY, cy, p.plane_bytes, 1);
-    for (int s = 0; s < kNumOut; ++s) place(kBufOut0 + s, co, p.plane_bytes, 1);
+    for (int s = 0; s < kMaxOut; ++s) place(kBufOut0 + s, s < p.n_out ? co : 0, p.plane_bytes, 1);
     off += kAlign;  // device status word
     if (out) *out = b;
     return (size_t)off;
@@ -209,7 +210,7 @@ bool build_forward_ooc_ex(const Plan& p, RunList& rl, size_t budget, const Forwa
                 int64_t h = (int64_t)p.r * (kk - m);
                 int64_t out_lo = last ? cg.s : std::max<int64_t>(0, cg.s - h);
                 int64_t out_hi = last ? cg.e : std::min<int64_t>(p.n0, cg.e + h);
-                int dst = last ? kBufOut0 + (int)(g % kNumOut) : ((j % 2 == 0) ? kBufX : kBufY);
+                int dst = last ? kBufOut0 + (int)(g % p.n_out) : ((j % 2 == 0) ? kBufX : kBufY);
                 // consecutive chunks alternate between two compute streams so
                 // that one chunk's last launch overlaps the next chunk's first
                 Op op = make_op(kOpKernel, (g % 2) ? kStreamCompute2 : kStreamCompute, t, i);
@@ -371,27 +372,42 @@ void trapezoid_work(const Plan& p, double* computed, double* useful) {
     *useful = u;
 }
 
+// Measured in-core rates (cell updates per second, in-plane halo work
+// included) of the kernels on one GB300: the register-streaming 3D star kernel
+// by radius and depth, and the generic kernel.
+double kernel_rate(const Plan& p, int depth) {
+    bool fast = p.kind == SO2DR_STAR && p.ndim == 3 && p.dtype != SO2DR_F64 && p.nx % 4 == 0 &&
+                depth <= p.max_kon_auto;
+    if (!fast) return p.dtype == SO2DR_F64 ? 20e9 : 100e9;
+    if (p.r == 1) {
+        const double r1[5] = {0, 512e9, 750e9, 990e9, 970e9};
+        return r1[std::min(depth, 4)];
+    }
+    if (p.r == 2) return depth >= 2 ? 450e9 : 380e9;
+    return p.r == 3 ? 320e9 : 280e9;
+}
+
 double predict_ms(const Plan& p) {
     double comp, use;
     trapezoid_work(p, &comp, &use);
-    double cells_plane = (double)p.plane_cells;
-    bool vc = p.kind == SO2DR_VARCOEF_STAR;
-    double in_plane_bytes = (double)p.plane_bytes + (vc ? 6.0 * cells_plane * 4 : 0.0);
-    double host_h2d = (double)p.rounds * p.n0 * in_plane_bytes / (p.bw_h2d * 1e9);
-    double host_d2h = (double)p.rounds * p.interior_planes() * p.plane_bytes / (p.bw_d2h * 1e9);
-    double host = std::max(host_h2d, host_d2h);
-    // in-plane overlapped tiling of a depth-k_on launch (tile 32 x 32)
-    double tile = 32.0, halo = (double)p.r * p.k_on;
-    double inplane = p.ndim == 3 ? ((tile + halo) * (tile + halo)) / (tile * tile)
-                                 : (256.0 + halo) / 256.0;
-    int npts = p.kind == SO2DR_VARCOEF_STAR ? 7 : num_coeffs(p.ndim, p.r, p.kind);
-    double flops = comp * cells_plane * inplane * (2.0 * npts);
-    double rate = (p.dtype == SO2DR_F64) ? 0.6e12 : 25e12;
-    double compute = flops / rate;
-    int L = (int)launch_depths(p.k_off, p.k_on).size();
-    double hbm = (double)p.rounds * p.n0 * p.plane_bytes * (2.0 + 2.0 * L) / (p.bw_hbm * 1e9);
-    double body = std::max(host, std::max(compute, hbm));
-    double fill = body / std::max(1, p.d * p.rounds) * 2.0;
+    const double cells_plane = (double)p.plane_cells;
+    const bool vc = p.kind == SO2DR_VARCOEF_STAR;
+    const double in_plane_bytes = (double)p.plane_bytes + (vc ? 6.0 * cells_plane * 4 : 0.0);
+    const double host_h2d = (double)p.rounds * p.n0 * in_plane_bytes / (p.bw_h2d * 1e9);
+    const double host_d2h = (double)p.rounds * p.interior_planes() * p.plane_bytes / (p.bw_d2h * 1e9);
+    // short out-of-core launches run at about 80% of the in-core rate
+    const double kernel = comp * cells_plane / (0.8 * kernel_rate(p, p.k_on));
+    const int L = (int)launch_depths(p.k_off, p.k_on).size();
+    const double units = (double)std::max(1, p.d * p.rounds);
+    const double t_launch = kernel / (units * L), t_d2h_chunk = host_d2h / units;
+    // without look-ahead a chunk's transfer waits for the previous chunk's
+    // first launch; with one output slab a chunk's last launch waits for the
+    // previous chunk's device-to-host copy
+    const double h2d_stall = p.lookahead ? 0.0 : units * t_launch;
+    const double out_stall = p.n_out >= 2 ? 0.0 : units * std::max(0.0, t_d2h_chunk - t_launch * (L - 1));
+    const double hbm = (double)p.rounds * p.n0 * p.plane_bytes * (2.0 + 2.0 * L) / (p.bw_hbm * 1e9);
+    const double body = std::max(std::max(host_h2d + h2d_stall, host_d2h), std::max(kernel + out_stall, hbm));
+    const double fill = body / units * 2.0;
     return (body + fill) * 1e3;
 }
 
@@ -504,23 +520,37 @@ int build_plan(Plan& p, int ndim, const int64_t* dims, int radius, int kind, con
             if (T > 64) koffs.push_back((int)std::min<int64_t>(T, 1 << 30));
         }
         double best = std::numeric_limits<double>::infinity();
-        int bko = 0, bkn = 0, bd = 0;
+        int bko = 0, bkn = 0, bd = 0, bla = 1, bno = 2;
+        // buffer options (look-ahead, output slabs); SO2DR_LOOKAHEAD / SO2DR_NOUT pin one
+        const char* ela = std::getenv("SO2DR_LOOKAHEAD");
+        const char* eno = std::getenv("SO2DR_NOUT");
+        std::vector<std::pair<int, int>> opts;
+        for (int la : {1, 0})
+            for (int no : {2, 1})
+                if ((!ela || std::atoi(ela) == la) && (!eno || std::atoi(eno) == no)) opts.push_back({la, no});
+        if (opts.empty()) opts.push_back({1, 2});
         for (int ko : koffs) {
             for (int kn : kons) {
                 if (kn > ko && koffs.size() > 1) continue;
-                Plan q = p;
-                q.k_off = ko;
-                q.k_on = std::min(kn, ko);
-                q.rounds = (int)((T + ko - 1) / ko);
-                int d = fit_chunks(q, min_chunks);
-                if (!d) continue;
-                double ms = predict_ms(q);
-                if (ms < best) { best = ms; bko = q.k_off; bkn = q.k_on; bd = d; }
+                for (auto [la, no] : opts) {
+                    Plan q = p;
+                    q.k_off = ko;
+                    q.k_on = std::min(kn, ko);
+                    q.rounds = (int)((T + ko - 1) / ko);
+                    q.lookahead = la;
+                    q.n_out = no;
+                    int d = fit_chunks(q, min_chunks);
+                    if (!d) continue;
+                    double ms = predict_ms(q);
+                    if (ms < best) { best = ms; bko = q.k_off; bkn = q.k_on; bd = d; bla = la; bno = no; }
+                }
             }
         }
         if (!bd) return fail(SO2DR_E_INFEASIBLE, "no chunking fits the device budget");
         p.k_off = bko;
         p.k_on = bkn;
+        p.lookahead = bla;
+        p.n_out = bno;
         p.rounds = (int)((T + bko - 1) / bko);
         p.d = bd;
         partition_planes(p);

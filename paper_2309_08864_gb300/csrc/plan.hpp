@@ -101,6 +101,8 @@ struct Plan {
     RunList ooc, ic;
     double redundancy = 0.0;
     int max_kon = kMaxKon;            // deepest fused launch the kernels support
+    int lookahead = 1;                // circular buffer holds the next chunk's new planes too (1) or not (0)
+    int n_out = 2;                    // output slabs (2: D2H of a chunk overlaps the next chunk's last launch)
     int max_kon_auto = kMaxKon;       // deepest launch the automatic choice considers
 
     int64_t interior_planes() const { return n0 - 2 * r; }

@@ -331,7 +331,7 @@ int execute(so2dr_plan_s* P, const RunList& rl, char* const* hosts, const int64_
 
 extern "C" {
 
-int so2dr_abi_version(void) { return 1; }
+int so2dr_abi_version(void) { return 2; }
 
 const char* so2dr_strerror(int status) {
     switch (status) {
@@ -437,6 +437,8 @@ int so2dr_plan_info(so2dr_plan_t P, so2dr_plan_info_t* info) {
     info->d2h_bytes_per_run = db;
     info->cell_updates_per_run = p.cell_updates();
     info->redundancy = p.redundancy;
+    info->lookahead = p.lookahead;
+    info->out_slabs = p.n_out;
     return SO2DR_OK;
 }
 

@@ -42,7 +42,8 @@ class PlanInfo(ctypes.Structure):
                 ("arena_bytes_in_core", ctypes.c_size_t), ("host_workspace_bytes", ctypes.c_size_t),
                 ("ops_per_run", ctypes.c_int64), ("launches_per_run", ctypes.c_int64),
                 ("h2d_bytes_per_run", ctypes.c_double), ("d2h_bytes_per_run", ctypes.c_double),
-                ("cell_updates_per_run", ctypes.c_double), ("redundancy", ctypes.c_double)]
+                ("cell_updates_per_run", ctypes.c_double), ("redundancy", ctypes.c_double),
+                ("lookahead", ctypes.c_int), ("out_slabs", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):

@@ -83,3 +83,23 @@ def test_emulator_detects_a_missing_wait():
             got = replay(p, u0, None, seed=sd, policy=pol)
             bad += not np.array_equal(got, ref)
     assert bad > 0
+
+
+@pytest.mark.parametrize("lookahead,nout", [(0, 1), (0, 2), (1, 1)])
+@pytest.mark.parametrize("case", [CASES[0], CASES[3], CASES[4], CASES[8], CASES[9]])
+def test_buffer_options_stay_race_free(case, lookahead, nout, monkeypatch):
+    """Without the one-chunk look-ahead and/or with a single output slab the
+    planner's waits must still order every reuse (random interleavings)."""
+    monkeypatch.setenv("SO2DR_LOOKAHEAD", str(lookahead))
+    monkeypatch.setenv("SO2DR_NOUT", str(nout))
+    dims, r, kind, T, dmin, kon, koff, budget = case
+    c, faces = _setup(dims, r, kind)
+    p = so2dr.Plan(dims, r, kind, c, T, min_chunks=dmin, k_on=kon, k_off=koff, budget_bytes=budget,
+                   dtype="f64")
+    assert p.info["lookahead"] == lookahead and p.info["out_slabs"] == nout
+    u0 = inputs.draw_box(1, dims)
+    ref = oracle.run_varcoef(u0, faces, T) if kind == "varcoef" else oracle.run(u0, c, r, 0 if kind == "star" else 1, T)
+    for sd in (0, 1):
+        assert np.array_equal(replay(p, u0, faces, seed=sd), ref)
+    for pol in ("h2d_first", "d2h_first"):
+        assert np.array_equal(replay(p, u0, faces, policy=pol), ref)
