@@ -14,6 +14,9 @@ region-sharing buffer, device-to-host transfers.
                   [--config c2|c1|c3|c4-bf16|c4-f16|c4-f32] [--k-off k] [--k-on k]
   python bench.py --kernel-case 512 --k-on 4      # in-core kernel run (profiling)
 
+k_off / k_on of 0 let the planner choose them (and its buffer options) from its
+cost model calibrated to the measured kernel rates.
+
 --impl reference times the FP64 CPU oracle (the only reference this method has:
 the paper ships no code) on the host cores, on bounded samples of the same
 workload.  Under torchrun (N > 1) every rank runs its own replica (the path
@@ -53,16 +56,16 @@ CONFIGS = {
                min_chunks=8, k_on=4, k_off=16),
     "c3": dict(workload="3D 25-point star r=4 FP32 1536^3 (14.5 GB), 32 steps, 4 GiB budget",
                dims=(1536, 1536, 1536), r=4, coeffs="r4", T=32, dtype="f32", budget=4 << 30,
-               min_chunks=1, k_on=1, k_off=8),
+               min_chunks=1, k_on=0, k_off=0),
     "c4-bf16": dict(workload="3D 7-point star BF16 storage 1024^3, 128 steps, 1 GiB budget",
                     dims=(1024, 1024, 1024), r=1, coeffs="star7", T=128, dtype="bf16",
-                    budget=1 << 30, min_chunks=8, k_on=4, k_off=16),
+                    budget=1 << 30, min_chunks=8, k_on=0, k_off=0),
     "c4-f16": dict(workload="3D 7-point star FP16 storage 1024^3, 128 steps, 1 GiB budget",
                    dims=(1024, 1024, 1024), r=1, coeffs="star7", T=128, dtype="f16",
-                   budget=1 << 30, min_chunks=8, k_on=4, k_off=16),
+                   budget=1 << 30, min_chunks=8, k_on=0, k_off=0),
     "c4-f32": dict(workload="3D 7-point star FP32 storage 1024^3, 128 steps, 1 GiB budget",
                    dims=(1024, 1024, 1024), r=1, coeffs="star7", T=128, dtype="f32",
-                   budget=1 << 30, min_chunks=8, k_on=4, k_off=12),
+                   budget=1 << 30, min_chunks=8, k_on=0, k_off=0),
     "c5": dict(workload="3D variable-coefficient 7-point FP32 512^3, 64 steps, adjoint with checkpoints "
                         "every 8 steps, 256 MiB budget",
                dims=(512, 512, 512), r=1, coeffs=None, T=64, dtype="f32", budget=256 << 20,

@@ -131,6 +131,7 @@ extern "C" int so2dr_run_device_noalloc(int ndim, const int64_t* dims, int radiu
         for (int k = 0; k < nc && k < kMaxCoeffsDev; ++k) {
             a.c[k] = coeffs[k];
             a.cf[k] = (float)coeffs[k];
+            a.cf2[k] = make_float2(a.cf[k], a.cf[k]);
         }
         cudaError_t e = launch_stencil(dtype, shape, radius, a, ls, static_cast<cudaStream_t>(stream));
         if (e != cudaSuccess) return cuda_fail(e, "stencil launch");

@@ -209,6 +209,7 @@ int enqueue_stencil(so2dr_plan_s* P, const RunList& rl, const Op& op, cudaStream
     for (size_t k = 0; k < p.coeffs.size() && k < (size_t)kMaxCoeffsDev; ++k) {
         a.c[k] = p.coeffs[k];
         a.cf[k] = (float)p.coeffs[k];
+        a.cf2[k] = make_float2(a.cf[k], a.cf[k]);
     }
     if (ls.fast) {
         // split axis 0 so the grid fills the SMs evenly

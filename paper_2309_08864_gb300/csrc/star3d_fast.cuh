@@ -136,7 +136,7 @@ struct FastTB {
     unsigned inyx;  // bit y*4+e: my cell is an interior cell of the plane
     const T* in;
     T* out;
-    float A[K][W2][VY][4];  // 2R partial sums per cell per level
+    float2 A[K][W2][VY][2];  // 2R partial sums per cell per level, in x pairs
 
     __device__ __forceinline__ explicit FastTB(const StencilArgs& args) : a(args) {}
 
@@ -161,16 +161,19 @@ struct FastTB {
     // -R..LYT+R-1 of the tile exist; those outside the tile hold garbage that
     // only reaches cells outside the level's valid area)
     template <int L, int PH, typename ST>
-    __device__ __forceinline__ void arrive(const float (&v)[VY][4], const ST* rows, int shift,
-                                           float (&done)[VY][4]) {
+    __device__ __forceinline__ void arrive(const float2 (&v)[VY][2], const ST* rows, int shift,
+                                           float2 (&done)[VY][2]) {
+        // x neighbours beyond my 4 cells, from the adjacent lanes
         float lft[VY][4], rgt[VY][4];
 #pragma unroll
         for (int y = 0; y < VY; ++y)
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
-                lft[y][e] = (e >= 4 - R) ? __shfl_up_sync(0xffffffffu, v[y][e], 1) : 0.f;
-                rgt[y][e] = (e < R) ? __shfl_down_sync(0xffffffffu, v[y][e], 1) : 0.f;
+                const float me = (e & 1) ? v[y][e >> 1].y : v[y][e >> 1].x;
+                lft[y][e] = (e >= 4 - R) ? __shfl_up_sync(0xffffffffu, me, 1) : 0.f;
+                rgt[y][e] = (e < R) ? __shfl_down_sync(0xffffffffu, me, 1) : 0.f;
             }
+        // y neighbours outside my VY rows, from shared memory
         float4 up[VY][R], dn[VY][R];
 #pragma unroll
         for (int y = 0; y < VY; ++y)
@@ -179,44 +182,59 @@ struct FastTB {
                 if (y - j < 0) up[y][j - 1] = lds4(rows + (my_row + y - j + shift) * LX + lane * 4);
                 if (y + j >= VY) dn[y][j - 1] = lds4(rows + (my_row + y + j + shift) * LX + lane * 4);
             }
-        // target t is plane zp - R + t, kept in slot (PH - R + t) mod 2R
+        // value of x neighbour e (-R..3+R) of row y, and the pair starting there
+        auto xval = [&](int y, int e) -> float {
+            if (e < 0) return lft[y][4 + e];
+            if (e > 3) return rgt[y][e - 4];
+            return (e & 1) ? v[y][e >> 1].y : v[y][e >> 1].x;
+        };
+        auto xpair = [&](int y, int e) -> float2 {
+            if (e == 0 || e == 2) return v[y][e >> 1];
+            return make_float2(xval(y, e), xval(y, e + 1));
+        };
+        auto ypair = [&](int y, int j, int h) -> float2 {  // row y + j (j may be out of my rows)
+            if (y + j >= 0 && y + j < VY) return v[y + j][h];
+            const float4 q = (j < 0) ? up[y][-j - 1] : dn[y][j - 1];
+            return h ? make_float2(q.z, q.w) : make_float2(q.x, q.y);
+        };
+        // target t is plane zp - R + t, kept in slot (PH - R + t) mod 2R.
+        // Cells are processed in x pairs with packed FP32x2 FMAs (each lane
+        // of a pair is an ordinary fused multiply-add rounded once, so the
+        // per-cell order below is the same as the scalar one).
 #pragma unroll
         for (int y = 0; y < VY; ++y)
 #pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const float x = v[y][e];
+            for (int h = 0; h < 2; ++h) {
+                const int e0 = 2 * h;
+                const float2 x = v[y][h];
 #pragma unroll
                 for (int t = R + 1; t < 2 * R; ++t) {
-                    float& acc = A[L][pmod(PH - R + t, W2)][y][e];
-                    acc = __fmaf_rn(a.cf[cidx<R>(0, -1, t - R)], x, acc);
+                    float2& acc = A[L][pmod(PH - R + t, W2)][y][h];
+                    acc = __ffma2_rn(a.cf2[cidx<R>(0, -1, t - R)], x, acc);
                 }
                 {
-                    float& acc = A[L][pmod(PH, W2)][y][e];
-                    float s = __fmaf_rn(a.cf[0], x, acc);
+                    float2& acc = A[L][pmod(PH, W2)][y][h];
+                    float2 s2 = __ffma2_rn(a.cf2[0], x, acc);
 #pragma unroll
                     for (int j = 1; j <= R; ++j) {
-                        float ym = (y - j >= 0) ? v[y - j][e] : f4get(up[y][j - 1], e);
-                        float yp = (y + j < VY) ? v[y + j][e] : f4get(dn[y][j - 1], e);
-                        s = __fmaf_rn(a.cf[cidx<R>(1, -1, j)], ym, s);
-                        s = __fmaf_rn(a.cf[cidx<R>(1, +1, j)], yp, s);
+                        s2 = __ffma2_rn(a.cf2[cidx<R>(1, -1, j)], ypair(y, -j, h), s2);
+                        s2 = __ffma2_rn(a.cf2[cidx<R>(1, +1, j)], ypair(y, +j, h), s2);
                     }
 #pragma unroll
                     for (int j = 1; j <= R; ++j) {
-                        float xm = (e - j >= 0) ? v[y][e - j] : lft[y][4 + e - j];
-                        float xp = (e + j < 4) ? v[y][e + j] : rgt[y][e + j - 4];
-                        s = __fmaf_rn(a.cf[cidx<R>(2, -1, j)], xm, s);
-                        s = __fmaf_rn(a.cf[cidx<R>(2, +1, j)], xp, s);
+                        s2 = __ffma2_rn(a.cf2[cidx<R>(2, -1, j)], xpair(y, e0 - j), s2);
+                        s2 = __ffma2_rn(a.cf2[cidx<R>(2, +1, j)], xpair(y, e0 + j), s2);
                     }
-                    acc = s;
+                    acc = s2;
                 }
 #pragma unroll
                 for (int t = 0; t < R; ++t) {
-                    float& acc = A[L][pmod(PH - R + t, W2)][y][e];
-                    acc = __fmaf_rn(a.cf[cidx<R>(0, +1, R - t)], x, acc);
+                    float2& acc = A[L][pmod(PH - R + t, W2)][y][h];
+                    acc = __ffma2_rn(a.cf2[cidx<R>(0, +1, R - t)], x, acc);
                 }
-                float& a0 = A[L][pmod(PH - R, W2)][y][e];
-                done[y][e] = a0;
-                a0 = a.cf[cidx<R>(0, -1, R)] * x;  // first contribution to target zp + R
+                float2& a0 = A[L][pmod(PH - R, W2)][y][h];
+                done[y][h] = a0;
+                a0 = __fmul2_rn(a.cf2[cidx<R>(0, -1, R)], x);  // first contribution to target zp + R
             }
     }
 
@@ -224,22 +242,23 @@ struct FastTB {
     // completion they take back the value they had at their centre arrival,
     // R phases ago, still resident in slot `cs` of the arrival planes.
     template <typename ST>
-    __device__ __forceinline__ void fixup(float (&done)[VY][4], int zt, const ST* cen) {
+    __device__ __forceinline__ void fixup(float2 (&done)[VY][2], int zt, const ST* cen) {
         const bool zbnd = zt < R || zt >= n0 - R;
         if (!(zbnd || warp_bnd)) return;
 #pragma unroll
         for (int y = 0; y < VY; ++y) {
             const unsigned rowmask = (inyx >> (y * 4)) & 0xFu;
             if (zbnd || rowmask != 0xFu) {
-                float4 q = lds4(cen + (my_row + y + R) * LX + lane * 4);
-#pragma unroll
-                for (int e = 0; e < 4; ++e)
-                    if (zbnd || !((rowmask >> e) & 1u)) done[y][e] = f4get(q, e);
+                const float4 q = lds4(cen + (my_row + y + R) * LX + lane * 4);
+                if (zbnd || !(rowmask & 1u)) done[y][0].x = q.x;
+                if (zbnd || !(rowmask & 2u)) done[y][0].y = q.y;
+                if (zbnd || !(rowmask & 4u)) done[y][1].x = q.z;
+                if (zbnd || !(rowmask & 8u)) done[y][1].y = q.w;
             }
         }
     }
 
-    __device__ __forceinline__ void emit(const float (&done)[VY][4], int zt) {
+    __device__ __forceinline__ void emit(const float2 (&done)[VY][2], int zt) {
         if (zt < olo || zt >= ohi) return;
         const int lx0 = lane * 4;
         if (!(lx0 >= S::HXA && lx0 < S::HXA + S::TX && xin)) return;
@@ -249,7 +268,7 @@ struct FastTB {
             int ty = my_row + y;
             int gy = ys + ty;
             if (ty >= S::HY && ty < S::HY + S::TY && gy < ny)
-                st4(ob + (int64_t)gy * nx + gx0, make_float4(done[y][0], done[y][1], done[y][2], done[y][3]));
+                st4(ob + (int64_t)gy * nx + gx0, make_float4(done[y][0].x, done[y][0].y, done[y][1].x, done[y][1].y));
         }
     }
 
@@ -266,13 +285,14 @@ struct FastTB {
             if constexpr (L + 1 < K) level<L + 1, PH>(p, sbuf, buf);
             return;
         }
-        float v[VY][4], done[VY][4];
+        float2 v[VY][2], done[VY][2];
         const int zt = za + p - L * (R + 1) - R;
         if constexpr (L == 0) {
 #pragma unroll
             for (int y = 0; y < VY; ++y) {
-                float4 q = lds4(sbuf + (my_row + y + R) * LX + lane * 4);
-                v[y][0] = q.x; v[y][1] = q.y; v[y][2] = q.z; v[y][3] = q.w;
+                const float4 q = lds4(sbuf + (my_row + y + R) * LX + lane * 4);
+                v[y][0] = make_float2(q.x, q.y);
+                v[y][1] = make_float2(q.z, q.w);
             }
             arrive<0, PH>(v, sbuf, R, done);
             fixup(done, zt, sin + ((p - R + NB * R) % NB) * INROWS * LX);
@@ -281,8 +301,9 @@ struct FastTB {
             const float* prev = slev + ((L - 1) * NB + pa) * LROWS * LX;
 #pragma unroll
             for (int y = 0; y < VY; ++y) {
-                float4 q = lds4(prev + (my_row + y + R) * LX + lane * 4);
-                v[y][0] = q.x; v[y][1] = q.y; v[y][2] = q.z; v[y][3] = q.w;
+                const float4 q = lds4(prev + (my_row + y + R) * LX + lane * 4);
+                v[y][0] = make_float2(q.x, q.y);
+                v[y][1] = make_float2(q.z, q.w);
             }
             arrive<L, pmod(PH - L * (R + 1), W2)>(v, prev, R, done);
             fixup(done, zt, slev + ((L - 1) * NB + (p - 1 - R + NB * (R + 1)) % NB) * LROWS * LX);
@@ -294,7 +315,7 @@ struct FastTB {
 #pragma unroll
             for (int y = 0; y < VY; ++y)
                 *reinterpret_cast<float4*>(lb + (my_row + y + R) * LX + lane * 4) =
-                    make_float4(done[y][0], done[y][1], done[y][2], done[y][3]);
+                    make_float4(done[y][0].x, done[y][0].y, done[y][1].x, done[y][1].y);
         }
         if constexpr (L + 1 < K) level<L + 1, PH>(p, sbuf, buf);
     }
@@ -350,7 +371,7 @@ struct FastTB {
 #pragma unroll
                 for (int y = 0; y < VY; ++y)
 #pragma unroll
-                    for (int e = 0; e < 4; ++e) A[l][q][y][e] = 0.f;
+                    for (int h = 0; h < 2; ++h) A[l][q][y][h] = make_float2(0.f, 0.f);
         // axis-0 segment of this CTA: outputs [zs, ze), stream over [za, zb)
         const int nseg = gridDim.z;
         const int nout = (int)(a.out_hi - a.out_lo), in_lo = (int)a.in_lo, in_hi = (int)a.in_hi;

@@ -42,7 +42,8 @@ struct StencilArgs {
     int tx, ty;           // output tile
     int* status;          // device status word (index checks)
     double c[kMaxCoeffsDev];
-    float cf[kMaxCoeffsDev];  // the same weights rounded once to FP32
+    float cf[kMaxCoeffsDev];   // the same weights rounded once to FP32
+    float2 cf2[kMaxCoeffsDev]; // (cf, cf) pairs for packed FP32x2 FMAs
 };
 
 template <typename T> struct Compute { using type = float; };
