@@ -90,18 +90,26 @@ def test_c4_precision_forms_1024cubed_128_steps():
         host, starts, info = _full_run(dims, r, coeffs, T, dtype, 1 << 30, 8, k_on=4, k_off=koff,
                                        in_core_check=(dtype == so2dr.BF16))
         rng = np.random.default_rng(0)
-        errs, l2n, l2d = [], 0.0, 0.0
+        errs, l2n, l2d, errs_u, l2n_u, l2d_u = [], 0.0, 0.0, [], 0.0, 0.0
         for lo, hi in sample_boxes(dims, starts, rng, n_random=0, w=2)[:3]:
             blo, bhi = oracle.cone_box(dims, lo, hi, r * T)
             u32 = inputs.draw_box(1, dims, blo, bhi, as_f32=True)
             ub = inputs.storage_to_f64(inputs.to_storage(u32.astype(np.float64), dtype), dtype)
             ref = oracle.run_cone(ub, gu.compute_coeffs(coeffs, dtype), r, oracle.STAR, T, blo, bhi, dims, lo, hi)
+            # also: the FP64 oracle from the unrounded draw with the exact weights
+            ref_u = oracle.run_cone(inputs.draw_box(1, dims, blo, bhi), coeffs, r, oracle.STAR, T, blo, bhi,
+                                    dims, lo, hi)
             got = gu.storage_of(host[tuple(slice(l, h) for l, h in zip(lo, hi))].contiguous(), dtype)
             errs.append(float(np.max(np.abs(got - ref)) / np.max(np.abs(ref))))
             l2n += float(np.sum((got - ref) ** 2))
             l2d += float(np.sum(ref ** 2))
+            errs_u.append(float(np.max(np.abs(got - ref_u)) / np.max(np.abs(ref_u))))
+            l2n_u += float(np.sum((got - ref_u) ** 2))
+            l2d_u += float(np.sum(ref_u ** 2))
         report[{so2dr.F32: "f32", so2dr.BF16: "bf16", so2dr.F16: "f16"}[dtype]] = {
-            "rel_linf": max(errs), "rel_l2": (l2n / l2d) ** 0.5, "k_off": info["k_off"], "chunks": info["chunks"]}
+            "rel_linf": max(errs), "rel_l2": (l2n / l2d) ** 0.5,
+            "rel_linf_vs_unrounded_draw": max(errs_u), "rel_l2_vs_unrounded_draw": (l2n_u / l2d_u) ** 0.5,
+            "k_off": info["k_off"], "chunks": info["chunks"]}
         assert max(errs) <= tol, (dtype, errs)
         del host
     print("PRECISION_REPORT " + json.dumps(report))
