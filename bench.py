@@ -348,6 +348,11 @@ def main():
     ap.add_argument("--radius", type=int, default=1)
     ap.add_argument("--launches", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--mode", default="so2dr", choices=["so2dr", "incore", "resreu"],
+                    help="so2dr: the out-of-core SO2DR pipeline (default); incore: the whole grid on the "
+                         "device, same launch depths, transfers outside the timed region; resreu: the "
+                         "redundancy-free out-of-core comparison code (single-step launches, region "
+                         "sharing of intermediate results)")
     args = ap.parse_args()
     cfg = dict(CONFIGS[args.config])
     if args.k_off is not None:
@@ -373,9 +378,10 @@ def main():
                       k_on=cfg["k_on"], k_off=cfg["k_off"], budget_bytes=cfg["budget"], dtype=cfg["dtype"],
                       link_gbs=(LINK_BIDIR_GBS / 2, LINK_BIDIR_GBS / 2), hbm_gbs=hbm_peak)
     info = plan.info
-    plan.bind()
+    mode = {"so2dr": 0, "incore": 1, "resreu": 2}[args.mode]
+    plan.bind(in_core=mode)
     for _ in range(args.warmup):
-        plan.run(host)
+        plan.run(host, in_core=mode)
     torch.cuda.synchronize()
     barrier(world)
     clocks = ClockSampler(local)
@@ -385,13 +391,17 @@ def main():
     t_all = time.perf_counter()
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        stats.append(plan.run(host))   # synchronous: joins every stream before returning
+        stats.append(plan.run(host, in_core=mode))   # synchronous: joins every stream before returning
         walls.append(time.perf_counter() - t0)
     torch.cuda.synchronize()
     t_all = time.perf_counter() - t_all
     barrier(world)
     clk = clocks.stop()
 
+    if mode == 1:
+        # in-core comparison code: transfers are excluded (Sec. V-D), time the kernels
+        for s_ in stats:
+            s_["total_ms"] = s_["kernel_ms"]
     dev_ms = sum(s["total_ms"] for s in stats)
     dev_ms_max = allreduce_max(dev_ms, world)
     wall_max = allreduce_max(sum(walls), world)
@@ -430,9 +440,10 @@ def main():
         "value": value, "unit": "Gcell/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": dev_ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": cfg["dtype"], "data": "synthetic (SplitMix64-seeded)",
-        "config": {"workload": cfg["workload"], "dims": list(cfg["dims"]), "radius": cfg["r"],
+        "config": {"workload": cfg["workload"], "mode": args.mode, "dims": list(cfg["dims"]), "radius": cfg["r"],
                    "time_steps": cfg["T"], "device_budget_bytes": cfg["budget"], "k_off": info["k_off"],
-                   "k_on": info["k_on"], "chunks": info["chunks"], "rounds": R,
+                   "k_on": info["k_on"] if mode != 2 else 1,
+                   "chunks": info["chunks"] if mode != 2 else info["result_reuse_chunks"], "rounds": R,
                    "ring_planes": info["ring_planes"], "arena_bytes": info["arena_bytes"],
                    "lookahead": info["lookahead"], "out_slabs": info["out_slabs"],
                    "redundancy": info["redundancy"], "parallelism": "replicas" if world > 1 else "1 GPU",

@@ -110,6 +110,8 @@ typedef struct {
                                 planes, so transfers run a chunk ahead of the kernels */
     int out_slabs;           /* output slabs (2: a chunk's device-to-host copy overlaps
                                 the next chunk's last launch)                        */
+    size_t arena_bytes_result_reuse; /* arena of mode 2 of so2dr_run (0: unavailable) */
+    int result_reuse_chunks; /* chunks mode 2 uses                                  */
 } so2dr_plan_info_t;
 
 /* Filled by so2dr_run / so2dr_adjoint when the caller passes a non-NULL pointer. */
@@ -136,7 +138,8 @@ typedef struct {
  * modulo the buffer's capacity.
  */
 typedef struct {
-    int kind;        /* 0 host-to-device copy, 1 kernel launch, 2 device-to-host copy */
+    int kind;        /* 0 host-to-device copy, 1 kernel launch, 2 device-to-host copy,
+                        3 on-device copy (region sharing of the result-reuse code)   */
     int stream;      /* 0 host-to-device, 1 compute (even chunks), 2 device-to-host,
                         3 compute (odd chunks)                                        */
     int round;
@@ -192,12 +195,12 @@ int so2dr_plan_info(so2dr_plan_t plan, so2dr_plan_info_t* info);
  * entries and covers [0, n0). */
 int so2dr_plan_chunks(so2dr_plan_t plan, int64_t* starts, int max_entries);
 
-/* Operation list of one run (in_core 0/1) in enqueue order.  With ops NULL the
- * call only reports the count in *n_ops. */
+/* Operation list of one run (mode 0/1/2 as in so2dr_run) in enqueue order.
+ * With ops NULL the call only reports the count in *n_ops. */
 int so2dr_plan_ops(so2dr_plan_t plan, int in_core, so2dr_op_t* ops, int64_t max_ops,
                    int64_t* n_ops);
 
-/* Arena regions used by the op list of one run (in_core 0/1). */
+/* Arena regions used by the op list of one run (mode 0/1/2). */
 int so2dr_plan_buffers(so2dr_plan_t plan, int in_core, so2dr_buffer_t* bufs, int max_bufs,
                        int* n_bufs);
 
@@ -227,11 +230,18 @@ int so2dr_bind(so2dr_plan_t plan, void* device_arena, size_t arena_bytes,
  *                  elements, updated in place.
  *   host_coeff_fields  VARCOEF_STAR only: the six face fields (see so2dr_kind),
  *                  read-only; NULL otherwise.
- *   in_core        0: out-of-core pipeline (chunks, circular region-sharing
- *                  buffer, trapezoids).  1: the whole grid is copied to the
- *                  device once, the same launch-depth sequence runs on it, and
- *                  it is copied back (the in-core comparison code of Sec. V-A);
- *                  the out-of-core result is bit-identical to it.
+ *   in_core        mode.  0: the out-of-core SO2DR pipeline (chunks, circular
+ *                  region-sharing buffer, trapezoids).  1: the whole grid is
+ *                  copied to the device once, the same launch-depth sequence
+ *                  runs on it, and it is copied back (the in-core comparison
+ *                  code of Sec. V-A); mode 0's result is bit-identical to it.
+ *                  2: the redundancy-free out-of-core code the paper compares
+ *                  against (result reuse, Sec. II-B Fig. 2b, Sec. V-A):
+ *                  single-step launches, region sharing of intermediate
+ *                  results before every step; same k_off rounds, its own
+ *                  chunking (plan_info().result_reuse_chunks) and arena
+ *                  (plan_info().arena_bytes_result_reuse); constant
+ *                  coefficients only.
  *   stats          optional timings.
  */
 int so2dr_run(so2dr_plan_t plan, void* host_grid, const void* host_coeff_fields, int in_core,
@@ -302,7 +312,7 @@ void so2dr_destroy(so2dr_plan_t plan);
 const char* so2dr_strerror(int status);
 const char* so2dr_last_error(void);
 
-/* ABI version of this header (bumped on any incompatible change): 2. */
+/* ABI version of this header (bumped on any incompatible change): 3. */
 int so2dr_abi_version(void);
 
 #ifdef __cplusplus

@@ -340,6 +340,168 @@ void build_forward_in_core(const Plan& p, RunList& rl) {
     }
 }
 
+// ----------------------------------------------------- result-reuse code
+
+namespace {
+
+// Buffers: slabs A/B for each of two chunk parities, the per-step ring for
+// each parity.
+enum { kRrA0 = 0, kRrB0 = 1, kRrA1 = 2, kRrB1 = 3, kRrRs0 = 4, kRrRs1 = 5 };
+
+size_t rr_layout(const Plan& p, std::vector<Buffer>* out) {
+    int64_t pmax = 0;
+    for (int i = 0; i < p.d; ++i) pmax = std::max(pmax, p.starts[i + 1] - p.starts[i]);
+    const int64_t slab = pmax + (int64_t)(p.k_off + 2) * p.r;     // planes a chunk's parallelogram spans
+    const int64_t ring = (int64_t)(p.k_off + 1) * 2 * p.r;         // top 2r planes of every step
+    std::vector<Buffer> b(6);
+    int64_t off = 0;
+    for (int id = 0; id < 6; ++id) {
+        int64_t cap = id < 4 ? slab : ring;
+        b[id] = {off, cap, p.plane_bytes, 1};
+        off += align_up(cap * p.plane_bytes);
+    }
+    off += kAlign;
+    if (out) *out = b;
+    return (size_t)off;
+}
+
+}  // namespace
+
+bool build_result_reuse(const Plan& p0, RunList& rl, size_t budget, int* chunks_out) {
+    if (p0.rounds <= 0 || p0.n0 - 2 * p0.r < 1) return false;
+    Plan p = p0;
+    // chunks: as few as fit the budget (at least the plan's floor)
+    int64_t M = p.n0 - 2 * p.r;
+    int d = std::max(1, p0.d);
+    for (; d <= M; ++d) {
+        p.d = d;
+        partition_planes(p);
+        if (!budget || rr_layout(p, nullptr) <= budget) break;
+    }
+    if (d > M) return false;
+    // region sharing of intermediate results needs every chunk to hold the
+    // parallelogram's shift plus the shared planes (the working space for
+    // halos may not exceed a chunk, Sec. IV-C)
+    for (int i = 0; i < p.d; ++i)
+        if (p.starts[i + 1] - p.starts[i] < (int64_t)(p.k_off + 2) * p.r) return false;
+    rl.ops.clear();
+    rl.arena_bytes = rr_layout(p, &rl.bufs);
+    const int nbuf = (int)rl.bufs.size();
+    Emitter em(rl, nbuf + 1, nbuf);
+    const int r = p.r;
+    int64_t g = 0;
+    for (int t = 0; t < p.rounds; ++t) {
+        const int kk = round_steps(p.T, p.k_off, t);
+        for (int i = 0; i < p.d; ++i, ++g) {
+            const int q = (int)(g % 2);
+            const int bufA = q ? kRrA1 : kRrA0, bufB = q ? kRrB1 : kRrB0;
+            const int ring_out = q ? kRrRs1 : kRrRs0, ring_in = q ? kRrRs0 : kRrRs1;
+            const bool first = i == 0, last = i == p.d - 1;
+            const int64_t s = p.starts[i], e = p.starts[i + 1];
+            // slot of plane z in the slabs: z - base (base = lowest plane ever held)
+            const int64_t base = std::max<int64_t>(0, s - (int64_t)(kk + 1) * r);
+            const int comp = (g % 2) ? kStreamCompute2 : kStreamCompute;
+            auto d2d = [&](int src, int64_t slo, int64_t sslot, int dst, int64_t dslot, int64_t n, int step) {
+                if (n <= 0) return;
+                Op op = make_op(kOpD2D, comp, t, i);
+                op.pub.depth = step;
+                op.pub.src_buf = src;
+                op.pub.src_lo = slo;
+                op.pub.src_hi = slo + n;
+                op.pub.src_slot0 = sslot;
+                op.pub.dst_buf = dst;
+                op.pub.dst_lo = slo;
+                op.pub.dst_hi = slo + n;
+                op.pub.dst_slot0 = dslot;
+                em.tr.access(src, sslot, sslot + n, false);
+                em.tr.access(dst, dslot, dslot + n, true);
+                em.emit(op);
+            };
+            // step 0: the chunk's own planes from the host
+            const int64_t hlo = first ? 0 : s, hhi = last ? p.n0 : e;
+            {
+                Op op = make_op(kOpH2D, kStreamH2D, t, i);
+                op.host_array = 0;
+                op.pub.src_lo = op.pub.dst_lo = hlo;
+                op.pub.src_hi = op.pub.dst_hi = hhi;
+                op.pub.src_slot0 = hlo;
+                op.pub.dst_buf = bufA;
+                op.pub.dst_slot0 = hlo - base;
+                em.tr.access(em.host_res(0), hlo, hhi, false);
+                em.tr.access(bufA, hlo - base, hhi - base, true);
+                em.emit(op);
+            }
+            int cur = bufA, oth = bufB;
+            // region sharing of step j: write my top 2r planes, read the previous chunk's
+            auto share = [&](int buf, int j) {
+                const int64_t top = last ? p.n0 : e - (int64_t)j * r;  // my range at step j ends here
+                if (!last) d2d(buf, top - 2 * r, top - 2 * r - base, ring_out, (int64_t)j * 2 * r, 2 * r, j);
+                if (!first) {
+                    const int64_t lo = s - (int64_t)(j + 2) * r;     // planes [s - (j+2)r, s - jr)
+                    const int64_t clo = std::max<int64_t>(0, lo);
+                    Op op = make_op(kOpD2D, comp, t, i);
+                    op.pub.depth = j;
+                    op.pub.src_buf = ring_in;
+                    op.pub.src_lo = clo;
+                    op.pub.src_hi = s - (int64_t)j * r;
+                    op.pub.src_slot0 = (int64_t)j * 2 * r + (clo - lo);
+                    op.pub.dst_buf = buf;
+                    op.pub.dst_lo = clo;
+                    op.pub.dst_hi = s - (int64_t)j * r;
+                    op.pub.dst_slot0 = clo - base;
+                    int64_t n = op.pub.src_hi - op.pub.src_lo;
+                    if (n > 0) {
+                        em.tr.access(ring_in, op.pub.src_slot0, op.pub.src_slot0 + n, false);
+                        em.tr.access(buf, op.pub.dst_slot0, op.pub.dst_slot0 + n, true);
+                        em.emit(op);
+                    }
+                }
+            };
+            share(cur, 0);
+            for (int j = 1; j <= kk; ++j) {
+                // step j: input planes [s-(j+1)r, e-(j-1)r) -> output [s-jr, e-jr)
+                const int64_t a = first ? 0 : s - (int64_t)(j + 1) * r;
+                const int64_t b = last ? p.n0 : e - (int64_t)(j - 1) * r;
+                const int64_t olo = first ? 0 : a + r, ohi = last ? p.n0 : b - r;
+                Op op = make_op(kOpKernel, comp, t, i);
+                op.fn = kFnStencil;
+                op.pub.depth = 1;
+                op.pub.edge_lo = a == 0;
+                op.pub.edge_hi = b == p.n0;
+                op.pub.src_buf = cur;
+                op.pub.src_lo = a;
+                op.pub.src_hi = b;
+                op.pub.src_slot0 = a - base;
+                op.pub.dst_buf = oth;
+                op.pub.dst_lo = olo;
+                op.pub.dst_hi = ohi;
+                op.pub.dst_slot0 = olo - base;
+                em.tr.access(cur, a - base, b - base, false);
+                em.tr.access(oth, olo - base, ohi - base, true);
+                em.emit(op);
+                std::swap(cur, oth);
+                if (j < kk) share(cur, j);
+            }
+            // back to the host: the final parallelogram's interior planes
+            const int64_t dlo = first ? r : s - (int64_t)kk * r, dhi = last ? p.n0 - r : e - (int64_t)kk * r;
+            if (dhi > dlo) {
+                Op op = make_op(kOpD2H, kStreamD2H, t, i);
+                op.host_array = 0;
+                op.pub.src_buf = cur;
+                op.pub.src_lo = op.pub.dst_lo = dlo;
+                op.pub.src_hi = op.pub.dst_hi = dhi;
+                op.pub.src_slot0 = dlo - base;
+                op.pub.dst_slot0 = dlo;
+                em.tr.access(cur, dlo - base, dhi - base, false);
+                em.tr.access(em.host_res(0), dlo, dhi, true);
+                em.emit(op);
+            }
+        }
+    }
+    if (chunks_out) *chunks_out = p.d;
+    return true;
+}
+
 // ------------------------------------------------------------- cost model
 
 namespace {
@@ -566,6 +728,8 @@ int build_plan(Plan& p, int ndim, const int64_t* dims, int radius, int kind, con
             return fail(SO2DR_E_INFEASIBLE, "the adjoint rounds do not fit the device budget");
     }
     build_forward_in_core(p, p.ic);
+    if (p.kind == SO2DR_STAR && p.rounds > 0)
+        if (!build_result_reuse(p, p.rr, p.budget, &p.rr_chunks)) p.rr_chunks = 0;
     int64_t cin, cx, cy, co;
     forward_caps(p, &cin, &cx, &cy, &co);
     p.ring_planes = cin;

@@ -17,7 +17,7 @@ namespace so2dr {
 
 // streams: host-to-device, compute (even chunks), device-to-host, compute (odd chunks)
 constexpr int kStreamH2D = 0, kStreamCompute = 1, kStreamD2H = 2, kStreamCompute2 = 3, kNumStreams = 4;
-constexpr int kOpH2D = 0, kOpKernel = 1, kOpD2H = 2;
+constexpr int kOpH2D = 0, kOpKernel = 1, kOpD2H = 2, kOpD2D = 3;
 constexpr int kHost = -1;           // buffer id of the host array of a copy
 constexpr int kMaxRadius = 4;
 constexpr int kMaxKon = 16;
@@ -99,6 +99,8 @@ struct Plan {
     double bw_h2d = 171.0, bw_d2h = 171.0, bw_hbm = 6781.0;
     // op lists of a forward run
     RunList ooc, ic;
+    RunList rr;                       // redundancy-free comparison code (result reuse), if it fits
+    int rr_chunks = 0;
     double redundancy = 0.0;
     int max_kon = kMaxKon;            // deepest fused launch the kernels support
     int lookahead = 1;                // circular buffer holds the next chunk's new planes too (1) or not (0)
@@ -128,6 +130,13 @@ int num_coeffs(int ndim, int radius, int kind);
 // buffers do not fit `budget` (budget 0 = unlimited).
 bool build_forward_ooc(const Plan& p, RunList& rl, size_t budget);
 void build_forward_in_core(const Plan& p, RunList& rl);
+
+// The redundancy-free out-of-core code the paper compares against (result
+// reuse, Sec. II-B Fig. 2b and Sec. V-A): single-step launches, each chunk a
+// parallelogram that shifts down by r per step and reads, before every step,
+// the previous chunk's top 2r planes of the previous step from a per-step
+// region-sharing ring.  Returns false if it does not fit `budget`.
+bool build_result_reuse(const Plan& p, RunList& rl, size_t budget, int* chunks_out);
 
 // Options of a forward op list used inside the adjoint pipeline.
 struct ForwardOpts {

@@ -175,7 +175,7 @@ int enqueue_stencil(so2dr_plan_s* P, const RunList& rl, const Op& op, cudaStream
         return set_error(SO2DR_E_DEVICE_CHECK, "kernel op ranges are inconsistent");
     const Buffer& bi = rl.bufs[o.src_buf];
     const Buffer& bo = rl.bufs[o.dst_buf];
-    if (o.src_hi - o.src_lo > bi.cap || o.dst_hi - o.dst_lo > bo.cap)
+    if (o.src_hi - o.src_lo > bi.cap || o.dst_slot0 < 0 || o.dst_slot0 + (o.dst_hi - o.dst_lo) > bo.cap)
         return set_error(SO2DR_E_DEVICE_CHECK, "kernel op exceeds its buffer");
     StencilArgs a;
     std::memset(&a, 0, sizeof(a));
@@ -184,7 +184,7 @@ int enqueue_stencil(so2dr_plan_s* P, const RunList& rl, const Op& op, cudaStream
     a.in_slot0 = o.src_slot0 % bi.cap;
     a.in_lo = o.src_lo;
     a.in_hi = o.src_hi;
-    a.out = P->arena + bo.offset;
+    a.out = P->arena + bo.offset + o.dst_slot0 * bo.plane_bytes;  // plane out_lo sits in slot dst_slot0
     a.out_lo = o.dst_lo;
     a.out_hi = o.dst_hi;
     if (op.aux_buf >= 0) {
@@ -258,7 +258,17 @@ int execute(so2dr_plan_s* P, const RunList& rl, char* const* hosts, const int64_
             if (e != cudaSuccess) return cuda_fail(e, "cudaStreamWaitEvent");
         }
         if (timing && (e = cudaEventRecord(P->tev[2 * j], s)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
-        if (o.kind == kOpH2D || o.kind == kOpD2H) {
+        if (o.kind == kOpD2D) {
+            const Buffer& bs = rl.bufs[o.src_buf];
+            const Buffer& bd = rl.bufs[o.dst_buf];
+            const int64_t n = o.src_hi - o.src_lo;
+            if (o.src_slot0 < 0 || o.dst_slot0 < 0 || o.src_slot0 + n > bs.cap || o.dst_slot0 + n > bd.cap)
+                return set_error(SO2DR_E_DEVICE_CHECK, "on-device copy exceeds its buffer");
+            e = cudaMemcpyAsync(P->arena + bd.offset + o.dst_slot0 * bd.plane_bytes,
+                                P->arena + bs.offset + o.src_slot0 * bs.plane_bytes, (size_t)(n * bs.plane_bytes),
+                                cudaMemcpyDeviceToDevice, s);
+            if (e != cudaSuccess) return cuda_fail(e, "on-device copy");
+        } else if (o.kind == kOpH2D || o.kind == kOpD2H) {
             bool h2d = o.kind == kOpH2D;
             int bid = h2d ? o.dst_buf : o.src_buf;
             const Buffer& b = rl.bufs[bid];
@@ -332,7 +342,7 @@ int execute(so2dr_plan_s* P, const RunList& rl, char* const* hosts, const int64_
 
 extern "C" {
 
-int so2dr_abi_version(void) { return 2; }
+int so2dr_abi_version(void) { return 3; }
 
 const char* so2dr_strerror(int status) {
     switch (status) {
@@ -440,6 +450,8 @@ int so2dr_plan_info(so2dr_plan_t P, so2dr_plan_info_t* info) {
     info->redundancy = p.redundancy;
     info->lookahead = p.lookahead;
     info->out_slabs = p.n_out;
+    info->arena_bytes_result_reuse = p.rr_chunks ? p.rr.arena_bytes : 0;
+    info->result_reuse_chunks = p.rr_chunks;
     return SO2DR_OK;
 }
 
@@ -452,7 +464,7 @@ int so2dr_plan_chunks(so2dr_plan_t P, int64_t* starts, int max_entries) {
 
 int so2dr_plan_ops(so2dr_plan_t P, int in_core, so2dr_op_t* ops, int64_t max_ops, int64_t* n_ops) {
     if (!P || !n_ops) return set_error(SO2DR_E_INVAL, "NULL argument");
-    const RunList& rl = in_core ? P->p.ic : P->p.ooc;
+    const RunList& rl = in_core == 2 ? P->p.rr : (in_core ? P->p.ic : P->p.ooc);
     *n_ops = (int64_t)rl.ops.size();
     if (!ops) return SO2DR_OK;
     if (max_ops < *n_ops) return set_error(SO2DR_E_INVAL, "ops array too small");
@@ -462,7 +474,7 @@ int so2dr_plan_ops(so2dr_plan_t P, int in_core, so2dr_op_t* ops, int64_t max_ops
 
 int so2dr_plan_buffers(so2dr_plan_t P, int in_core, so2dr_buffer_t* bufs, int max_bufs, int* n_bufs) {
     if (!P || !n_bufs) return set_error(SO2DR_E_INVAL, "NULL argument");
-    const RunList& rl = in_core ? P->p.ic : P->p.ooc;
+    const RunList& rl = in_core == 2 ? P->p.rr : (in_core ? P->p.ic : P->p.ooc);
     *n_bufs = (int)rl.bufs.size();
     if (!bufs) return SO2DR_OK;
     if (max_bufs < *n_bufs) return set_error(SO2DR_E_INVAL, "bufs array too small");
@@ -531,7 +543,10 @@ int so2dr_run(so2dr_plan_t P, void* host_grid, const void* host_coeff_fields, in
         rc = check_pinned(host_coeff_fields, "host_coeff_fields");
         if (rc) return rc;
     }
-    const RunList& rl = in_core ? p.ic : p.ooc;
+    if (in_core < 0 || in_core > 2) return set_error(SO2DR_E_INVAL, "mode must be 0, 1 or 2");
+    if (in_core == 2 && p.rr_chunks == 0)
+        return set_error(SO2DR_E_UNSUPPORTED, "the result-reuse code needs a constant-coefficient plan that fits");
+    const RunList& rl = in_core == 2 ? p.rr : (in_core ? p.ic : p.ooc);
     char* hosts[2] = {static_cast<char*>(host_grid), const_cast<char*>(static_cast<const char*>(host_coeff_fields))};
     int64_t cb = p.dtype == SO2DR_F64 ? 8 : 4;
     int64_t hpb[2] = {p.plane_bytes, p.plane_cells * cb};

@@ -43,7 +43,8 @@ class PlanInfo(ctypes.Structure):
                 ("ops_per_run", ctypes.c_int64), ("launches_per_run", ctypes.c_int64),
                 ("h2d_bytes_per_run", ctypes.c_double), ("d2h_bytes_per_run", ctypes.c_double),
                 ("cell_updates_per_run", ctypes.c_double), ("redundancy", ctypes.c_double),
-                ("lookahead", ctypes.c_int), ("out_slabs", ctypes.c_int)]
+                ("lookahead", ctypes.c_int), ("out_slabs", ctypes.c_int),
+                ("arena_bytes_result_reuse", ctypes.c_size_t), ("result_reuse_chunks", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -214,10 +215,13 @@ class Plan:
 
     # ------------------------------------------------------------ execution
     def bind(self, in_core=False, arena=None, streams=None):
-        """Lends a torch device arena and four torch streams to the plan."""
+        """Lends a torch device arena and four torch streams to the plan
+        (in_core: 0 out-of-core, 1 in-core, 2 the result-reuse code)."""
         import torch
         info = self.info
-        need = info["arena_bytes_in_core"] if in_core else info["arena_bytes"]
+        mode = int(in_core)
+        need = (info["arena_bytes_in_core"] if mode == 1 else
+                info["arena_bytes_result_reuse"] if mode == 2 else info["arena_bytes"])
         if self.kind == VARCOEF_STAR and not in_core and self._budget:
             # the adjoint's pipelines fit their own chunkings into the bound arena
             need = max(need, self._budget)
@@ -230,12 +234,12 @@ class Plan:
                                          arena.numel() * arena.element_size(), hs, len(streams)))
         self._arena = arena
         self._streams = streams
-        self._bound_in_core = bool(in_core)
+        self._bound_in_core = mode
         return self
 
     def run(self, host_grid, coeff_fields=None, in_core=False, stats=True):
         """Advances host_grid (pinned CPU tensor of the plan's dtype) in place."""
-        if self._arena is None or (in_core and not self._bound_in_core):
+        if self._arena is None or int(in_core) != self._bound_in_core:
             self.bind(in_core=in_core)
         st = Stats()
         _check(load_library().so2dr_run(self._h, _ptr(host_grid), _ptr(coeff_fields), int(in_core),
@@ -244,7 +248,7 @@ class Plan:
 
     def adjoint(self, u0, coeff_fields, target, grad_u0, grad_coeffs, workspace, checkpoint_every=8,
                 stats=True):
-        if self._arena is None:
+        if self._arena is None or self._bound_in_core != 0:
             self.bind()
         loss = ctypes.c_double()
         st = Stats()

@@ -38,10 +38,14 @@ def replay(plan, u0, coeff_fields=None, in_core=False, seed=0, policy="random"):
             lo, hi = o["src_lo"], o["src_hi"]
             b = o["dst_buf"]
             sl = slots(o["dst_slot0"], hi - lo, bufs[b][1])
-            if kind == 2 and b == (1 if not in_core else 1) and cdev is not None and _is_coef(o, in_core):
+            if kind == 2 and cdev is not None and _is_coef(o, in_core):
                 cdev[b][:, sl] = coeff_fields[:, lo:hi]
             else:
                 dev[b][sl] = host[lo:hi]
+        elif k == 3:  # device -> device (region sharing of the result-reuse code)
+            n = o["src_hi"] - o["src_lo"]
+            sb, db = o["src_buf"], o["dst_buf"]
+            dev[db][slots(o["dst_slot0"], n, bufs[db][1])] = dev[sb][slots(o["src_slot0"], n, bufs[sb][1])]
         elif k == 2:  # device -> host
             lo, hi = o["src_lo"], o["src_hi"]
             b = o["src_buf"]

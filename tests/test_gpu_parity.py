@@ -114,3 +114,27 @@ def test_varcoef_forward(dtype):
     dims = (40, 36, 34)
     faces = np.stack([inputs.draw_box(100 + f, dims, a=0.05, b=0.15) for f in range(6)])
     check_case(dims, 1, "varcoef", None, 9, dtype, 4, 3, 5, 0, faces=faces)
+
+
+@pytest.mark.parametrize("dims,r,T,koff,kon,budget", [((96, 80, 132), 1, 12, 6, 3, 8 << 20),
+                                                      ((120, 64, 128), 2, 8, 4, 2, 16 << 20),
+                                                      ((160, 40, 256), 1, 10, 10, 4, 8 << 20)])
+def test_result_reuse_code_matches_in_core(dims, r, T, koff, kon, budget):
+    """Mode 2 (the redundancy-free comparison code: single-step launches,
+    region sharing of intermediate results) computes the same cells as the
+    in-core run: FP32 storage keeps every level in FP32 either way."""
+    import torch
+    c = [0.4] + [0.1] * 6 if r == 1 else _coeffs(3, r, "star")
+    u = inputs.draw_box(1, dims, as_f32=True)
+    p = so2dr.Plan(dims, r, "star", c, T, min_chunks=4, k_on=kon, k_off=koff, budget_bytes=budget, dtype="f32")
+    assert p.info["result_reuse_chunks"] >= 2
+    rr = torch.from_numpy(u.copy()).pin_memory()
+    ic = torch.from_numpy(u.copy()).pin_memory()
+    oc = torch.from_numpy(u.copy()).pin_memory()
+    p.run(rr, in_core=2)
+    p.run(ic, in_core=1)
+    p.run(oc, in_core=0)
+    assert torch.equal(rr, ic) and torch.equal(oc, ic)
+    ref = oracle.run(u.astype(np.float64), gu.compute_coeffs(c, so2dr.F32), r, 0, T)
+    assert gu.rel_linf(rr.numpy().astype(np.float64), ref) <= 1e-5
+    p.close()

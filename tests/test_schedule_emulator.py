@@ -103,3 +103,28 @@ def test_buffer_options_stay_race_free(case, lookahead, nout, monkeypatch):
         assert np.array_equal(replay(p, u0, faces, seed=sd), ref)
     for pol in ("h2d_first", "d2h_first"):
         assert np.array_equal(replay(p, u0, faces, policy=pol), ref)
+
+
+@pytest.mark.parametrize("case", [CASES[0], CASES[1], CASES[2], CASES[3], CASES[5], CASES[6], CASES[8], CASES[10]])
+def test_result_reuse_code_is_exact(case):
+    """The redundancy-free comparison code (single-step launches, region
+    sharing of intermediate results before every step) computes the same
+    values as the in-core oracle, in any interleaving the waits allow."""
+    dims, r, kind, T, dmin, kon, koff, budget = case
+    c, faces = _setup(dims, r, kind)
+    p = so2dr.Plan(dims, r, kind, c, T, min_chunks=dmin, k_on=kon, k_off=koff, budget_bytes=budget, dtype="f64")
+    info = p.info
+    starts = p.chunks()
+    if info["result_reuse_chunks"] == 0:
+        # unavailable exactly when some chunk cannot hold the parallelogram's shift
+        assert np.min(np.diff(starts)) < (koff + 2) * r or info["rounds"] == 0
+        return
+    if budget:
+        assert info["arena_bytes_result_reuse"] <= budget
+    ops = p.ops(2)
+    assert all(o["depth"] == 1 for o in ops if o["kind"] == 1)   # single-step kernels only
+    u0 = inputs.draw_box(1, dims)
+    ref = oracle.run(u0, c, r, 0 if kind == "star" else 1, T)
+    for sd in (0, 1):
+        assert np.array_equal(replay(p, u0, None, in_core=2, seed=sd), ref)
+    assert np.array_equal(replay(p, u0, None, in_core=2, policy="h2d_first"), ref)
