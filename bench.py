@@ -335,6 +335,50 @@ def run_adjoint(args, cfg, world, rank, local):
     return 0
 
 
+def run_sweep(args, cfg, coeffs, host, hbm_peak, rank):
+    """Run-time tuning trade-off (Sec. V-B, Fig. 5): one plan per k_off (k_on and
+    the buffer options as the planner picks them for that k_off, or --k-on),
+    each run warmup + steps times; least measured time beside the model's
+    prediction, the chunk count and redundancy the budget forces, and the
+    stage times."""
+    from paper_2309_08864_gb300 import so2dr
+    link = (LINK_BIDIR_GBS / 2, LINK_BIDIR_GBS / 2)
+    rows = []
+    for ko in [int(x) for x in args.sweep.split(",") if x]:
+        kon = args.k_on or 0
+        try:
+            plan = so2dr.Plan(cfg["dims"], cfg["r"], "star", coeffs, cfg["T"], min_chunks=cfg["min_chunks"],
+                              k_on=kon, k_off=ko, budget_bytes=cfg["budget"], dtype=cfg["dtype"], link_gbs=link,
+                              hbm_gbs=hbm_peak)
+        except so2dr.So2drError as e:
+            rows.append({"k_off": ko, "status": str(e)})
+            continue
+        info = plan.info
+        pred = so2dr.candidates(cfg["dims"], cfg["r"], "star", coeffs, cfg["T"], min_chunks=cfg["min_chunks"],
+                                k_on=info["k_on"], k_off=ko, budget_bytes=cfg["budget"], dtype=cfg["dtype"],
+                                link_gbs=link, hbm_gbs=hbm_peak)
+        pred_ms = [e["predicted_ms"] for e in pred if e["lookahead"] == info["lookahead"] and
+                   e["out_slabs"] == info["out_slabs"]][0]
+        plan.bind()
+        best = None
+        for i in range(args.warmup + args.steps):
+            st = plan.run(host)
+            if i >= args.warmup and (best is None or st["total_ms"] < best["total_ms"]):
+                best = st
+        rows.append({"k_off": ko, "k_on": info["k_on"], "chunks": info["chunks"], "rounds": info["rounds"],
+                     "lookahead": info["lookahead"], "out_slabs": info["out_slabs"],
+                     "redundancy": round(info["redundancy"], 4), "predicted_ms": round(pred_ms, 2),
+                     "measured_ms": round(best["total_ms"], 2),
+                     "gcells_per_s": round(info["cell_updates_per_run"] / (best["total_ms"] * 1e-3) / 1e9, 1),
+                     "kernel_ms": round(best["kernel_ms"], 2), "h2d_ms": round(best["h2d_ms"], 2),
+                     "d2h_ms": round(best["d2h_ms"], 2)})
+        plan.close()
+    if rank == 0:
+        print(json.dumps({"sweep": rows, "workload": cfg["workload"], "steps": args.steps,
+                          "warmup": args.warmup}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -353,6 +397,12 @@ def main():
                          "device, same launch depths, transfers outside the timed region; resreu: the "
                          "redundancy-free out-of-core comparison code (single-step launches, region "
                          "sharing of intermediate results)")
+    ap.add_argument("--tune", type=int, default=0,
+                    help="measured autotune before timing: time the model's N best plans (so2dr_autotune) "
+                         "and benchmark the fastest")
+    ap.add_argument("--sweep", default="",
+                    help="comma-separated k_off values: measured and predicted time of one run per k_off "
+                         "(the run-time tuning trade-off of Sec. V-B); prints one JSON line")
     args = ap.parse_args()
     cfg = dict(CONFIGS[args.config])
     if args.k_off is not None:
@@ -374,9 +424,25 @@ def main():
     hbm_peak, peak_kind = measured_peaks()
     coeffs = coeffs_of(cfg["coeffs"], inputs)
     host = make_input(cfg, inputs, so2dr, torch)
-    plan = so2dr.Plan(cfg["dims"], cfg["r"], "star", coeffs, cfg["T"], min_chunks=cfg["min_chunks"],
-                      k_on=cfg["k_on"], k_off=cfg["k_off"], budget_bytes=cfg["budget"], dtype=cfg["dtype"],
-                      link_gbs=(LINK_BIDIR_GBS / 2, LINK_BIDIR_GBS / 2), hbm_gbs=hbm_peak)
+    if args.sweep:
+        return run_sweep(args, cfg, coeffs, host, hbm_peak, rank)
+    tuned = None
+    if args.tune > 0:
+        # the timings do not depend on the values: the benchmark grid is the scratch
+        table, link = so2dr.autotune(cfg["dims"], cfg["r"], "star", coeffs, cfg["T"], cfg["budget"], cfg["dtype"],
+                                     scratch=host, max_candidates=args.tune, repeats=2,
+                                     min_chunks=cfg["min_chunks"], k_on=cfg["k_on"] if args.k_on else 0,
+                                     k_off=cfg["k_off"] if args.k_off else 0)
+        tuned = {"candidates_timed": args.tune, "link_gbs": {"h2d": link[0], "d2h": link[1], "hbm": link[2]},
+                 "table": [[e["k_off"], e["k_on"], e["chunks"], e["lookahead"], e["out_slabs"],
+                            round(e["predicted_ms"], 2), round(e["measured_ms"], 2)] for e in table[:args.tune]],
+                 "columns": ["k_off", "k_on", "chunks", "lookahead", "out_slabs", "predicted_ms", "measured_ms"]}
+        plan = so2dr.Plan(cfg["dims"], cfg["r"], "star", coeffs, cfg["T"], budget_bytes=cfg["budget"],
+                          dtype=cfg["dtype"], tune_entry=table[0])
+    else:
+        plan = so2dr.Plan(cfg["dims"], cfg["r"], "star", coeffs, cfg["T"], min_chunks=cfg["min_chunks"],
+                          k_on=cfg["k_on"], k_off=cfg["k_off"], budget_bytes=cfg["budget"], dtype=cfg["dtype"],
+                          link_gbs=(LINK_BIDIR_GBS / 2, LINK_BIDIR_GBS / 2), hbm_gbs=hbm_peak)
     info = plan.info
     mode = {"so2dr": 0, "incore": 1, "resreu": 2}[args.mode]
     plan.bind(in_core=mode)
@@ -468,6 +534,8 @@ def main():
                               "h2d": sum(s["h2d_ms"] for s in stats) / args.steps,
                               "d2h": sum(s["d2h_ms"] for s in stats) / args.steps},
     }
+    if tuned:
+        line["autotune"] = tuned
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         from paper_2309_08864_gb300 import inputs as _inp
         import oracle

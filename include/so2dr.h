@@ -204,6 +204,44 @@ int so2dr_plan_ops(so2dr_plan_t plan, int in_core, so2dr_op_t* ops, int64_t max_
 int so2dr_plan_buffers(so2dr_plan_t plan, int in_core, so2dr_buffer_t* bufs, int max_bufs,
                        int* n_bufs);
 
+/*
+ * One point of the run-time parameter search (Sec. IV-C chooses d, k_off and
+ * k_on so that kernel time and transfer time balance under the device
+ * capacity; Sec. V-B's Fig. 5 measures that trade-off).
+ */
+typedef struct {
+    int k_off;           /* steps per round                                      */
+    int k_on;            /* steps fused per launch                               */
+    int chunks;          /* d: the fewest chunks whose buffers fit the budget    */
+    int lookahead;       /* circular buffer also holds the next chunk's planes   */
+    int out_slabs;       /* output slabs (1 or 2)                                */
+    int status;          /* SO2DR_OK, or why the candidate could not be timed    */
+    double predicted_ms; /* cost model's time of one run                         */
+    double measured_ms;  /* least measured time of one run; -1 if not timed      */
+} so2dr_tune_entry_t;
+
+/*
+ * Every feasible (k_off, k_on, look-ahead, output slabs) point of the
+ * planner's search for this problem, with its chunk count and predicted time,
+ * sorted by predicted time (host only; no CUDA call).  Arguments as in
+ * so2dr_plan_ex; k_on or k_off non-zero pins that parameter.  Writes at most
+ * table_cap entries; *table_len receives how many exist.
+ */
+int so2dr_plan_candidates(int ndim, const int64_t* dims, int radius, int kind, const double* coeffs,
+                          int ncoeffs, int64_t time_steps, int min_chunks, int k_on, int k_off,
+                          size_t device_budget_bytes, int storage, double link_h2d_gbs,
+                          double link_d2h_gbs, double hbm_gbs, so2dr_tune_entry_t* table,
+                          int table_cap, int* table_len);
+
+/*
+ * Builds the plan of one table entry (its k_off, k_on, chunks, lookahead and
+ * out_slabs; host only).  Returns SO2DR_E_INFEASIBLE if it does not fit the
+ * budget.
+ */
+int so2dr_plan_tuned(so2dr_plan_t* out, int ndim, const int64_t* dims, int radius, int kind,
+                     const double* coeffs, int ncoeffs, int64_t time_steps,
+                     const so2dr_tune_entry_t* entry, size_t device_budget_bytes, int storage);
+
 /* ------------------------------------------------------------- execution */
 
 /*
@@ -246,6 +284,30 @@ int so2dr_bind(so2dr_plan_t plan, void* device_arena, size_t arena_bytes,
  */
 int so2dr_run(so2dr_plan_t plan, void* host_grid, const void* host_coeff_fields, int in_core,
               so2dr_stats_t* stats);
+
+/*
+ * Measured autotune of the run-time parameters (Sec. IV-C's choice of d,
+ * k_off and k_on, made by timing instead of by the model alone).
+ *   1. Measures the host link (host-to-device and device-to-host copies of
+ *      up to 1 GiB between scratch_host_grid and the arena, each alone, best
+ *      of 3) and HBM (an on-device copy inside the arena); link_gbs receives
+ *      {h2d, d2h, hbm} in GB/s (may be NULL).
+ *   2. Ranks the candidates of so2dr_plan_candidates with those rates.
+ *   3. Runs the best max_candidates of them (mode 0) on scratch_host_grid,
+ *      each `repeats` times, with the given arena and streams.
+ * scratch_host_grid is a pinned host grid of the problem's shape and dtype
+ * whose contents are overwritten (the timings do not depend on its values);
+ * device_arena must hold device_budget_bytes.  The table (at most table_cap
+ * entries) is sorted by measured time, untimed entries last; build the
+ * winner with so2dr_plan_tuned(table[0]).  Plain problems only (no
+ * VARCOEF_STAR).  Synchronises the streams.
+ */
+int so2dr_autotune(int ndim, const int64_t* dims, int radius, int kind, const double* coeffs,
+                   int ncoeffs, int64_t time_steps, int min_chunks, int k_on, int k_off,
+                   size_t device_budget_bytes, int storage, void* device_arena,
+                   void* const* cuda_streams, int nstreams, void* scratch_host_grid,
+                   int max_candidates, int repeats, so2dr_tune_entry_t* table, int table_cap,
+                   int* table_len, double* link_gbs);
 
 /*
  * Gradient of L = 1/2 ||u_T - u*||^2 (T = time_steps) for a VARCOEF_STAR plan,

@@ -611,7 +611,8 @@ static int fit_chunks(Plan& p, int dmin) {
 
 int build_plan(Plan& p, int ndim, const int64_t* dims, int radius, int kind, const double* coeffs,
                int ncoeffs, int64_t T, int min_chunks, int k_on, int k_off, size_t budget,
-               int dtype, double bw_h2d, double bw_d2h, double bw_hbm, std::string* err) {
+               int dtype, double bw_h2d, double bw_d2h, double bw_hbm, std::string* err,
+               const PlanSearch* search) {
     auto fail = [&](int code, const char* m) { if (err) *err = m; return code; };
     if (ndim != 2 && ndim != 3) return fail(SO2DR_E_INVAL, "ndim must be 2 or 3");
     if (!dims) return fail(SO2DR_E_INVAL, "dims is NULL");
@@ -686,10 +687,12 @@ int build_plan(Plan& p, int ndim, const int64_t* dims, int radius, int kind, con
         // buffer options (look-ahead, output slabs); SO2DR_LOOKAHEAD / SO2DR_NOUT pin one
         const char* ela = std::getenv("SO2DR_LOOKAHEAD");
         const char* eno = std::getenv("SO2DR_NOUT");
+        const int fla = search && search->lookahead >= 0 ? search->lookahead : (ela ? std::atoi(ela) : -1);
+        const int fno = search && search->n_out >= 0 ? search->n_out : (eno ? std::atoi(eno) : -1);
         std::vector<std::pair<int, int>> opts;
         for (int la : {1, 0})
             for (int no : {2, 1})
-                if ((!ela || std::atoi(ela) == la) && (!eno || std::atoi(eno) == no)) opts.push_back({la, no});
+                if ((fla < 0 || fla == la) && (fno < 0 || fno == no)) opts.push_back({la, no});
         if (opts.empty()) opts.push_back({1, 2});
         for (int ko : koffs) {
             for (int kn : kons) {
@@ -704,6 +707,16 @@ int build_plan(Plan& p, int ndim, const int64_t* dims, int radius, int kind, con
                     int d = fit_chunks(q, min_chunks);
                     if (!d) continue;
                     double ms = predict_ms(q);
+                    if (search && search->ranked) {
+                        Candidate c;
+                        c.k_off = q.k_off;
+                        c.k_on = q.k_on;
+                        c.d = d;
+                        c.lookahead = la;
+                        c.n_out = no;
+                        c.predicted_ms = ms;
+                        search->ranked->push_back(c);
+                    }
                     if (ms < best) { best = ms; bko = q.k_off; bkn = q.k_on; bd = d; bla = la; bno = no; }
                 }
             }

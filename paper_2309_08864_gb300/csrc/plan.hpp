@@ -111,10 +111,26 @@ struct Plan {
     double cell_updates() const;
 };
 
+// One point of the planner's search: schedule parameters and the cost
+// model's predicted time of a run.
+struct Candidate {
+    int k_off = 1, k_on = 1, d = 1, lookahead = 1, n_out = 2;
+    double predicted_ms = 0.0;
+};
+
+// Search controls: pin the buffer options (-1 = choose; they override the
+// SO2DR_LOOKAHEAD / SO2DR_NOUT variables) and, if `ranked` is set, collect
+// every feasible candidate of the search (in search order).
+struct PlanSearch {
+    int lookahead = -1, n_out = -1;
+    std::vector<Candidate>* ranked = nullptr;
+};
+
 // Builds a plan; returns SO2DR_OK or an error code (message in *err).
 int build_plan(Plan& p, int ndim, const int64_t* dims, int radius, int kind, const double* coeffs,
                int ncoeffs, int64_t T, int min_chunks, int k_on, int k_off, size_t budget,
-               int dtype, double bw_h2d, double bw_d2h, double bw_hbm, std::string* err);
+               int dtype, double bw_h2d, double bw_d2h, double bw_hbm, std::string* err,
+               const PlanSearch* search = nullptr);
 
 // Launch-depth sequence of a round of k steps with k_on-step kernels
 // (Algorithm 1: floor(k/k_on) k_on-step launches, then one (k mod k_on)-step).

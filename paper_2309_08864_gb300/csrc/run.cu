@@ -338,11 +338,51 @@ int execute(so2dr_plan_s* P, const RunList& rl, char* const* hosts, const int64_
 
 }  // namespace so2dr
 
+namespace so2dr {
+
+int plan_create(so2dr_plan_t* out, int ndim, const int64_t* dims, int radius, int kind, const double* coeffs,
+                int ncoeffs, int64_t time_steps, int min_chunks, int k_on, int k_off, size_t device_budget_bytes,
+                int storage, double link_h2d_gbs, double link_d2h_gbs, double hbm_gbs, const PlanSearch* search) {
+    if (!out) return set_error(SO2DR_E_INVAL, "out is NULL");
+    *out = nullptr;
+    so2dr_plan_s* P = new (std::nothrow) so2dr_plan_s();
+    if (!P) return set_error(SO2DR_E_NOMEM, "plan allocation failed");
+    std::string err;
+    int csize = storage == SO2DR_F64 ? 8 : 4;
+    int shape = kind == SO2DR_VARCOEF_STAR ? kVarcoef3D : kind == SO2DR_BOX ? kBox2D : (ndim == 3 ? kStar3D : kStar2D);
+    int maxd = (radius >= 1 && radius <= kMaxRadius) ? stencil_max_depth(shape, radius, csize) : kMaxKon;
+    int rc;
+    try {
+        P->p.max_kon = maxd;
+        // the automatic choice stays within the register-streaming kernel when
+        // it covers this stencil (the generic kernel is far slower)
+        if (shape == kStar3D && storage != SO2DR_F64 && ndim == 3 && dims && dims[2] % 4 == 0) {
+            int fm = 0;
+            for (int d = 1; d <= kMaxKon; ++d)
+                if (fast_star3d_supported(radius, d)) fm = d;
+            if (fm > 0) P->p.max_kon_auto = fm;
+        }
+        rc = build_plan(P->p, ndim, dims, radius, kind, coeffs, ncoeffs, time_steps, min_chunks, k_on, k_off,
+                        device_budget_bytes, storage, link_h2d_gbs, link_d2h_gbs, hbm_gbs, &err, search);
+    } catch (const std::bad_alloc&) {
+        delete P;
+        return set_error(SO2DR_E_NOMEM, "host allocation failed while planning");
+    }
+    if (rc) {
+        delete P;
+        return set_error(rc, err);
+    }
+    *out = P;
+    return SO2DR_OK;
+}
+
+}  // namespace so2dr
+
 // ==================================================================== C ABI
 
 extern "C" {
 
-int so2dr_abi_version(void) { return 3; }
+int so2dr_abi_version(void) { return 4; }
 
 const char* so2dr_strerror(int status) {
     switch (status) {
@@ -366,37 +406,8 @@ int so2dr_plan_ex(so2dr_plan_t* out, int ndim, const int64_t* dims, int radius, 
                   const double* coeffs, int ncoeffs, int64_t time_steps, int min_chunks, int k_on,
                   int k_off, size_t device_budget_bytes, int storage, double link_h2d_gbs,
                   double link_d2h_gbs, double hbm_gbs) {
-    if (!out) return set_error(SO2DR_E_INVAL, "out is NULL");
-    *out = nullptr;
-    so2dr_plan_s* P = new (std::nothrow) so2dr_plan_s();
-    if (!P) return set_error(SO2DR_E_NOMEM, "plan allocation failed");
-    std::string err;
-    int csize = storage == SO2DR_F64 ? 8 : 4;
-    int shape = kind == SO2DR_VARCOEF_STAR ? kVarcoef3D : kind == SO2DR_BOX ? kBox2D : (ndim == 3 ? kStar3D : kStar2D);
-    int maxd = (radius >= 1 && radius <= kMaxRadius) ? stencil_max_depth(shape, radius, csize) : kMaxKon;
-    int rc;
-    try {
-        P->p.max_kon = maxd;
-        // the automatic choice stays within the register-streaming kernel when
-        // it covers this stencil (the generic kernel is far slower)
-        if (shape == kStar3D && storage != SO2DR_F64 && ndim == 3 && dims && dims[2] % 4 == 0) {
-            int fm = 0;
-            for (int d = 1; d <= kMaxKon; ++d)
-                if (fast_star3d_supported(radius, d)) fm = d;
-            if (fm > 0) P->p.max_kon_auto = fm;
-        }
-        rc = build_plan(P->p, ndim, dims, radius, kind, coeffs, ncoeffs, time_steps, min_chunks, k_on, k_off,
-                        device_budget_bytes, storage, link_h2d_gbs, link_d2h_gbs, hbm_gbs, &err);
-    } catch (const std::bad_alloc&) {
-        delete P;
-        return set_error(SO2DR_E_NOMEM, "host allocation failed while planning");
-    }
-    if (rc) {
-        delete P;
-        return set_error(rc, err);
-    }
-    *out = P;
-    return SO2DR_OK;
+    return so2dr::plan_create(out, ndim, dims, radius, kind, coeffs, ncoeffs, time_steps, min_chunks, k_on,
+                              k_off, device_budget_bytes, storage, link_h2d_gbs, link_d2h_gbs, hbm_gbs, nullptr);
 }
 
 int so2dr_plan(so2dr_plan_t* out, int ndim, const int64_t* dims, int radius, int kind, const double* coeffs,

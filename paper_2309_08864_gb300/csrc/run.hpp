@@ -47,4 +47,9 @@ int execute(so2dr_plan_s* P, const RunList& rl, char* const* hosts, const int64_
 
 size_t adjoint_workspace_bytes(const Plan& p);
 
+// so2dr_plan_ex with search controls (pinned buffer options, candidate list).
+int plan_create(so2dr_plan_t* out, int ndim, const int64_t* dims, int radius, int kind, const double* coeffs,
+                int ncoeffs, int64_t time_steps, int min_chunks, int k_on, int k_off, size_t device_budget_bytes,
+                int storage, double link_h2d_gbs, double link_d2h_gbs, double hbm_gbs, const PlanSearch* search);
+
 }  // namespace so2dr

@@ -23,7 +23,7 @@ OK, E_INVAL, E_INFEASIBLE, E_NOT_BOUND, E_CUDA, E_TIMEOUT, E_DEVICE_CHECK, E_NOM
 SYMBOLS = ["so2dr_plan", "so2dr_plan_ex", "so2dr_plan_info", "so2dr_plan_chunks", "so2dr_plan_ops",
            "so2dr_plan_buffers", "so2dr_bind", "so2dr_run", "so2dr_adjoint", "so2dr_loss", "so2dr_dot",
            "so2dr_destroy", "so2dr_strerror", "so2dr_last_error", "so2dr_abi_version",
-           "so2dr_run_device_noalloc"]
+           "so2dr_run_device_noalloc", "so2dr_plan_candidates", "so2dr_plan_tuned", "so2dr_autotune"]
 
 
 class So2drError(RuntimeError):
@@ -65,6 +65,12 @@ class OpRec(ctypes.Structure):
                 ("wait_op", ctypes.c_int64 * 4)]
 
 
+class TuneEntry(ctypes.Structure):
+    _fields_ = [("k_off", ctypes.c_int), ("k_on", ctypes.c_int), ("chunks", ctypes.c_int),
+                ("lookahead", ctypes.c_int), ("out_slabs", ctypes.c_int), ("status", ctypes.c_int),
+                ("predicted_ms", ctypes.c_double), ("measured_ms", ctypes.c_double)]
+
+
 class BufRec(ctypes.Structure):
     _fields_ = [("offset_bytes", ctypes.c_int64), ("capacity_planes", ctypes.c_int64)]
 
@@ -102,6 +108,14 @@ def load_library(path=None):
     lib.so2dr_loss.argtypes = [vp, vp, vp, vp, vp, c_size, dp]
     lib.so2dr_dot.argtypes = [vp, vp, vp, i64, c_int, dp]
     lib.so2dr_run_device_noalloc.argtypes = [c_int, i64p, c_int, c_int, dp, c_int, i64, c_int, c_int, vp, vp, vp]
+    tep = ctypes.POINTER(TuneEntry)
+    lib.so2dr_plan_candidates.argtypes = [c_int, i64p, c_int, c_int, dp, c_int, i64, c_int, c_int, c_int,
+                                          c_size, c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                          tep, c_int, ctypes.POINTER(c_int)]
+    lib.so2dr_plan_tuned.argtypes = [planp, c_int, i64p, c_int, c_int, dp, c_int, i64, tep, c_size, c_int]
+    lib.so2dr_autotune.argtypes = [c_int, i64p, c_int, c_int, dp, c_int, i64, c_int, c_int, c_int, c_size,
+                                   c_int, vp, ctypes.POINTER(vp), c_int, vp, c_int, c_int, tep, c_int,
+                                   ctypes.POINTER(c_int), dp]
     lib.so2dr_destroy.argtypes = [vp]
     lib.so2dr_destroy.restype = None
     lib.so2dr_strerror.argtypes = [c_int]
@@ -140,7 +154,9 @@ class Plan:
 
     def __init__(self, dims, radius=1, kind="star", coeffs=None, time_steps=1, min_chunks=1,
                  k_on=0, k_off=0, budget_bytes=1 << 30, dtype="f32", link_gbs=(0.0, 0.0),
-                 hbm_gbs=0.0):
+                 hbm_gbs=0.0, tune_entry=None):
+        """tune_entry: a row of candidates()/autotune() (so2dr_plan_tuned);
+        it replaces min_chunks, k_on, k_off and the link rates."""
         lib = load_library()
         self.kind = KINDS[kind] if isinstance(kind, str) else int(kind)
         self.dtype = DTYPES[dtype] if isinstance(dtype, str) else int(dtype)
@@ -150,10 +166,16 @@ class Plan:
         h = ctypes.c_void_p()
         d = (ctypes.c_int64 * len(self.dims))(*self.dims)
         cp = None if c is None else c.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
-        rc = lib.so2dr_plan_ex(ctypes.byref(h), len(self.dims), d, int(radius), self.kind, cp,
-                               0 if c is None else int(c.size), int(time_steps), int(min_chunks),
-                               int(k_on), int(k_off), int(budget_bytes), self.dtype,
-                               float(link_gbs[0]), float(link_gbs[1]), float(hbm_gbs))
+        nc = 0 if c is None else int(c.size)
+        if tune_entry is not None:
+            e = _entry_struct(tune_entry)
+            rc = lib.so2dr_plan_tuned(ctypes.byref(h), len(self.dims), d, int(radius), self.kind, cp, nc,
+                                      int(time_steps), ctypes.byref(e), int(budget_bytes), self.dtype)
+        else:
+            rc = lib.so2dr_plan_ex(ctypes.byref(h), len(self.dims), d, int(radius), self.kind, cp, nc,
+                                   int(time_steps), int(min_chunks), int(k_on), int(k_off),
+                                   int(budget_bytes), self.dtype, float(link_gbs[0]), float(link_gbs[1]),
+                                   float(hbm_gbs))
         _check(rc)
         self._h = h
         self._budget = int(budget_bytes)
@@ -284,6 +306,63 @@ class Plan:
         dt = F64 if str(a.dtype).endswith("float64") else F32
         _check(load_library().so2dr_dot(self._h, _ptr(a), _ptr(b), int(a.numel()), dt, ctypes.byref(out)))
         return out.value
+
+
+def _entry_struct(e):
+    t = TuneEntry()
+    for k, _ in TuneEntry._fields_:
+        setattr(t, k, e.get(k, -1.0 if k == "measured_ms" else 0))
+    return t
+
+
+def _problem(dims, kind, coeffs):
+    dims = tuple(int(x) for x in dims)
+    c = None if coeffs is None else np.ascontiguousarray(coeffs, dtype=np.float64)
+    cp = None if c is None else c.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    return (dims, (ctypes.c_int64 * len(dims))(*dims), KINDS[kind] if isinstance(kind, str) else int(kind),
+            c, cp, 0 if c is None else int(c.size))
+
+
+def candidates(dims, radius=1, kind="star", coeffs=None, time_steps=1, min_chunks=1, k_on=0, k_off=0,
+               budget_bytes=1 << 30, dtype="f32", link_gbs=(0.0, 0.0), hbm_gbs=0.0):
+    """Every feasible point of the planner's search, cheapest predicted first
+    (so2dr_plan_candidates; host only)."""
+    lib = load_library()
+    dims, d, kd, c, cp, nc = _problem(dims, kind, coeffs)
+    dt = DTYPES[dtype] if isinstance(dtype, str) else int(dtype)
+    n = ctypes.c_int()
+    args = [len(dims), d, int(radius), kd, cp, nc, int(time_steps), int(min_chunks), int(k_on), int(k_off),
+            int(budget_bytes), dt, float(link_gbs[0]), float(link_gbs[1]), float(hbm_gbs)]
+    _check(lib.so2dr_plan_candidates(*args, None, 0, ctypes.byref(n)))
+    arr = (TuneEntry * max(1, n.value))()
+    _check(lib.so2dr_plan_candidates(*args, arr, n.value, ctypes.byref(n)))
+    return [{k: getattr(e, k) for k, _ in TuneEntry._fields_} for e in arr[:n.value]]
+
+
+def autotune(dims, radius=1, kind="star", coeffs=None, time_steps=1, budget_bytes=1 << 30, dtype="f32",
+             scratch=None, arena=None, streams=None, max_candidates=8, repeats=2, min_chunks=1, k_on=0,
+             k_off=0):
+    """Measured autotune (so2dr_autotune): returns (table sorted by measured
+    time, (h2d, d2h, hbm) GB/s).  scratch is a pinned host grid of the
+    problem's shape and dtype; its contents are overwritten."""
+    import torch
+    lib = load_library()
+    dims, d, kd, c, cp, nc = _problem(dims, kind, coeffs)
+    dt = DTYPES[dtype] if isinstance(dtype, str) else int(dtype)
+    if arena is None:
+        arena = torch.empty(int(budget_bytes), dtype=torch.uint8, device="cuda")
+    if streams is None:
+        streams = [torch.cuda.Stream() for _ in range(4)]
+    hs = (ctypes.c_void_p * len(streams))(*[ctypes.c_void_p(s.cuda_stream) for s in streams])
+    cap = 4096
+    arr = (TuneEntry * cap)()
+    n = ctypes.c_int()
+    link = (ctypes.c_double * 3)()
+    _check(lib.so2dr_autotune(len(dims), d, int(radius), kd, cp, nc, int(time_steps), int(min_chunks), int(k_on),
+                              int(k_off), int(budget_bytes), dt, ctypes.c_void_p(arena.data_ptr()), hs,
+                              len(streams), _ptr(scratch), int(max_candidates), int(repeats), arr, cap,
+                              ctypes.byref(n), link))
+    return [{k: getattr(e, k) for k, _ in TuneEntry._fields_} for e in arr[:min(cap, n.value)]], tuple(link)
 
 
 def _varcoef_loss_fn():
