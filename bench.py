@@ -66,6 +66,38 @@ CONFIGS = {
     "c4-f32": dict(workload="3D 7-point star FP32 storage 1024^3, 128 steps, 1 GiB budget",
                    dims=(1024, 1024, 1024), r=1, coeffs="star7", T=128, dtype="f32",
                    budget=1 << 30, min_chunks=8, k_on=0, k_off=0),
+    "box2d1r": dict(workload="2D 9-point box (radius 1) FP32 38400^2 (5.9 GB), 640 steps, 4 GiB budget "
+                             "(the paper's box2d1r workload, seeded weights)",
+                    dims=(38400, 38400), r=1, kind="box", coeffs="box1", T=640, dtype="f32", budget=4 << 30,
+                    min_chunks=1, k_on=0, k_off=0),
+    "box2d2r": dict(workload="2D 25-point box (radius 2) FP32 38400^2 (5.9 GB), 640 steps, 4 GiB budget "
+                             "(the paper's box2d2r workload, seeded weights)",
+                    dims=(38400, 38400), r=2, kind="box", coeffs="box2", T=640, dtype="f32", budget=4 << 30,
+                    min_chunks=1, k_on=0, k_off=0),
+    "box2d3r": dict(workload="2D 49-point box (radius 3) FP32 38400^2 (5.9 GB), 640 steps, 4 GiB budget "
+                             "(the paper's box2d3r workload, seeded weights)",
+                    dims=(38400, 38400), r=3, kind="box", coeffs="box3", T=640, dtype="f32", budget=4 << 30,
+                    min_chunks=1, k_on=0, k_off=0),
+    "box2d4r": dict(workload="2D 81-point box (radius 4) FP32 38400^2 (5.9 GB), 640 steps, 4 GiB budget "
+                             "(the paper's box2d4r workload, seeded weights)",
+                    dims=(38400, 38400), r=4, kind="box", coeffs="box4", T=640, dtype="f32", budget=4 << 30,
+                    min_chunks=1, k_on=0, k_off=0),
+    "box2d1r-ic": dict(workload="2D 9-point box (radius 1) FP32 12800^2 (the paper's in-core dataset), 640 "
+                                "steps, at least 4 chunks under a 1 GiB budget",
+                       dims=(12800, 12800), r=1, kind="box", coeffs="box1", T=640, dtype="f32", budget=1 << 30,
+                       min_chunks=4, k_on=0, k_off=0),
+    "box2d2r-ic": dict(workload="2D 25-point box (radius 2) FP32 12800^2 (the paper's in-core dataset), 640 "
+                                "steps, at least 4 chunks under a 1 GiB budget",
+                       dims=(12800, 12800), r=2, kind="box", coeffs="box2", T=640, dtype="f32", budget=1 << 30,
+                       min_chunks=4, k_on=0, k_off=0),
+    "box2d3r-ic": dict(workload="2D 49-point box (radius 3) FP32 12800^2 (the paper's in-core dataset), 640 "
+                                "steps, at least 4 chunks under a 1 GiB budget",
+                       dims=(12800, 12800), r=3, kind="box", coeffs="box3", T=640, dtype="f32", budget=1 << 30,
+                       min_chunks=4, k_on=0, k_off=0),
+    "box2d4r-ic": dict(workload="2D 81-point box (radius 4) FP32 12800^2 (the paper's in-core dataset), 640 "
+                                "steps, at least 4 chunks under a 1 GiB budget",
+                       dims=(12800, 12800), r=4, kind="box", coeffs="box4", T=640, dtype="f32", budget=1 << 30,
+                       min_chunks=4, k_on=0, k_off=0),
     "c5": dict(workload="3D variable-coefficient 7-point FP32 512^3, 64 steps, adjoint with checkpoints "
                         "every 8 steps, 256 MiB budget",
                dims=(512, 512, 512), r=1, coeffs=None, T=64, dtype="f32", budget=256 << 20,
@@ -74,6 +106,8 @@ CONFIGS = {
 
 
 def coeffs_of(name, inputs):
+    if name.startswith("box"):
+        return list(inputs.box2d_coeffs(int(name[3:])))
     if name == "jacobi2d":
         return [0.2] * 5
     if name == "star7":
@@ -183,7 +217,7 @@ def oracle_sample(cfg, inputs, steps=None, planes=None):
     sub = (n0,) + tuple(dims[1:])
     u = inputs.draw_box(1, dims, lo=(0,) * nd, hi=sub)
     c = coeffs_of(cfg["coeffs"], inputs)
-    kind = 0
+    kind = 1 if cfg.get("kind") == "box" else 0
     t0 = time.perf_counter()
     oracle.run(u, c, cfg["r"], kind, T)
     dt = time.perf_counter() - t0
@@ -265,17 +299,24 @@ def run_kernel_case(args):
     from paper_2309_08864_gb300 import inputs, so2dr
     n = args.kernel_case
     r = args.radius
-    coeffs = [0.4] + [0.1] * 6 if r == 1 else list(inputs.radius4_star_coeffs())
     kon = args.k_on or 4
     T = kon * max(1, args.launches)
-    u = torch.from_numpy(inputs.draw_box(1, (n, n, n), as_f32=True)).pin_memory()
-    plan = so2dr.Plan((n, n, n), r, "star", coeffs, T, min_chunks=1, k_on=kon, k_off=T, budget_bytes=0,
-                      dtype="f32")
+    if args.kind == "box":
+        dims, kind, coeffs = (n, n), "box", list(inputs.box2d_coeffs(r))
+    else:
+        dims, kind = (n, n, n), "star"
+        coeffs = [0.4] + [0.1] * 6 if r == 1 else list(inputs.radius4_star_coeffs())
+    cells = 1
+    for e in dims:
+        cells *= e
+    u = torch.from_numpy(inputs.draw_box(1, dims, as_f32=True)).pin_memory()
+    plan = so2dr.Plan(dims, r, kind, coeffs, T, min_chunks=1, k_on=kon, k_off=T, budget_bytes=0, dtype="f32")
     for _ in range(max(1, args.warmup) + args.steps):
         st = plan.run(u, in_core=True)
-    print(json.dumps({"kernel_case": n, "radius": r, "k_on": kon, "launches": st["launches"],
-                      "kernel_ms_per_launch": st["kernel_ms"] / st["launches"],
-                      "alg_GBs": 2 * 4 * n ** 3 / (st["kernel_ms"] / st["launches"] * 1e-3) / 1e9}))
+    ms = st["kernel_ms"] / st["launches"]
+    print(json.dumps({"kernel_case": n, "kind": kind, "radius": r, "k_on": kon, "launches": st["launches"],
+                      "kernel_ms_per_launch": ms, "alg_GBs": 2 * 4 * cells / (ms * 1e-3) / 1e9,
+                      "gcell_steps_per_s": cells * kon / (ms * 1e-3) / 1e9}))
     return 0
 
 
@@ -347,14 +388,14 @@ def run_sweep(args, cfg, coeffs, host, hbm_peak, rank):
     for ko in [int(x) for x in args.sweep.split(",") if x]:
         kon = args.k_on or 0
         try:
-            plan = so2dr.Plan(cfg["dims"], cfg["r"], "star", coeffs, cfg["T"], min_chunks=cfg["min_chunks"],
+            plan = so2dr.Plan(cfg["dims"], cfg["r"], cfg.get("kind", "star"), coeffs, cfg["T"], min_chunks=cfg["min_chunks"],
                               k_on=kon, k_off=ko, budget_bytes=cfg["budget"], dtype=cfg["dtype"], link_gbs=link,
                               hbm_gbs=hbm_peak)
         except so2dr.So2drError as e:
             rows.append({"k_off": ko, "status": str(e)})
             continue
         info = plan.info
-        pred = so2dr.candidates(cfg["dims"], cfg["r"], "star", coeffs, cfg["T"], min_chunks=cfg["min_chunks"],
+        pred = so2dr.candidates(cfg["dims"], cfg["r"], cfg.get("kind", "star"), coeffs, cfg["T"], min_chunks=cfg["min_chunks"],
                                 k_on=info["k_on"], k_off=ko, budget_bytes=cfg["budget"], dtype=cfg["dtype"],
                                 link_gbs=link, hbm_gbs=hbm_peak)
         pred_ms = [e["predicted_ms"] for e in pred if e["lookahead"] == info["lookahead"] and
@@ -390,6 +431,7 @@ def main():
     ap.add_argument("--k-on", type=int, default=None)
     ap.add_argument("--kernel-case", type=int, default=0)
     ap.add_argument("--radius", type=int, default=1)
+    ap.add_argument("--kind", default="star", choices=["star", "box"], help="--kernel-case stencil (box: 2D n x n)")
     ap.add_argument("--launches", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--mode", default="so2dr", choices=["so2dr", "incore", "resreu"],
@@ -429,7 +471,7 @@ def main():
     tuned = None
     if args.tune > 0:
         # the timings do not depend on the values: the benchmark grid is the scratch
-        table, link = so2dr.autotune(cfg["dims"], cfg["r"], "star", coeffs, cfg["T"], cfg["budget"], cfg["dtype"],
+        table, link = so2dr.autotune(cfg["dims"], cfg["r"], cfg.get("kind", "star"), coeffs, cfg["T"], cfg["budget"], cfg["dtype"],
                                      scratch=host, max_candidates=args.tune, repeats=2,
                                      min_chunks=cfg["min_chunks"], k_on=cfg["k_on"] if args.k_on else 0,
                                      k_off=cfg["k_off"] if args.k_off else 0)
@@ -437,10 +479,10 @@ def main():
                  "table": [[e["k_off"], e["k_on"], e["chunks"], e["lookahead"], e["out_slabs"],
                             round(e["predicted_ms"], 2), round(e["measured_ms"], 2)] for e in table[:args.tune]],
                  "columns": ["k_off", "k_on", "chunks", "lookahead", "out_slabs", "predicted_ms", "measured_ms"]}
-        plan = so2dr.Plan(cfg["dims"], cfg["r"], "star", coeffs, cfg["T"], budget_bytes=cfg["budget"],
+        plan = so2dr.Plan(cfg["dims"], cfg["r"], cfg.get("kind", "star"), coeffs, cfg["T"], budget_bytes=cfg["budget"],
                           dtype=cfg["dtype"], tune_entry=table[0])
     else:
-        plan = so2dr.Plan(cfg["dims"], cfg["r"], "star", coeffs, cfg["T"], min_chunks=cfg["min_chunks"],
+        plan = so2dr.Plan(cfg["dims"], cfg["r"], cfg.get("kind", "star"), coeffs, cfg["T"], min_chunks=cfg["min_chunks"],
                           k_on=cfg["k_on"], k_off=cfg["k_off"], budget_bytes=cfg["budget"], dtype=cfg["dtype"],
                           link_gbs=(LINK_BIDIR_GBS / 2, LINK_BIDIR_GBS / 2), hbm_gbs=hbm_peak)
     info = plan.info
@@ -524,8 +566,10 @@ def main():
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                      "frac": achieved / hbm_peak,
                      "traffic": (DRAM_PER_ALG_BYTE_R1K4_F32 * io_bytes / max(1, n_main)
-                                 if (cfg["r"], info["k_on"], cfg["dtype"]) == (1, 4, "f32") else None),
-                     "kernel": "star3d_fast_kernel (k_on-step TB launch)", "peak_kind": peak_kind + " (burst)",
+                                 if (cfg.get("kind", "star"), len(cfg["dims"]), cfg["r"], info["k_on"],
+                                     cfg["dtype"]) == ("star", 3, 1, 4, "f32") else None),
+                     "kernel": ("box2d_fast_kernel" if cfg.get("kind") == "box" else "star3d_fast_kernel")
+                               + " (k_on-step TB launch)", "peak_kind": peak_kind + " (burst)",
                      "avg_launch_ms": avg_launch_s * 1e3, "launches": mk_n},
         "e2e": {"value": e2e, "unit": "Gcell/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": int(sum(s["launches"] for s in stats)),

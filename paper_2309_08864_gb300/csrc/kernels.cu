@@ -1,5 +1,6 @@
 // kernels.cu -- launch geometry and dtype dispatch of the stencil kernel.
 #include "kernels.hpp"
+#include "box2d_fast.cuh"
 #include "star3d_fast.cuh"
 
 #include <cstdlib>
@@ -24,7 +25,25 @@ bool fast_star3d_supported(int r, int depth) {
            ((r == 3 || r == 4) && depth == 1);
 }
 
+bool fast_box2d_supported(int r, int depth) {
+    return depth >= 1 && ((r == 1 && depth <= 8) || (r == 2 && depth <= 4) || (r == 3 && depth <= 3) ||
+                          (r == 4 && depth <= 2));
+}
+
 namespace {
+template <int R, int K> void box_shape(LaunchShape& ls, int64_t nx, int esize) {
+    using S = BoxShape<R, K>;
+    ls.lx = S::LX;
+    ls.ly = 1;
+    ls.tx = S::TX;
+    ls.ty = 1;
+    ls.block = dim3(S::NT, 1, 1);
+    ls.smem = esize == 4 ? S::template smem<4>() : S::template smem<2>();
+    ls.grid = dim3((unsigned)((nx + S::TX - 1) / S::TX), 1, 1);
+    ls.ok = true;
+    ls.fast = kFastBox2D;
+}
+
 template <int R, int K> void fast_shape(LaunchShape& ls, int64_t ny, int64_t nx, int esize) {
     using S = FastShape<R, K>;
     ls.lx = S::LX;
@@ -35,15 +54,38 @@ template <int R, int K> void fast_shape(LaunchShape& ls, int64_t ny, int64_t nx,
     ls.smem = esize == 4 ? S::template smem<4>() : S::template smem<2>();
     ls.grid = dim3((unsigned)((nx + S::TX - 1) / S::TX), (unsigned)((ny + S::TY - 1) / S::TY), 1);
     ls.ok = ls.grid.y <= 65535;
-    ls.fast = true;
+    ls.fast = kFastStar3D;
 }
 }  // namespace
 
 LaunchShape stencil_launch_shape(int shape, int r, int depth, int64_t ny, int64_t nx, int csize, int esize) {
     LaunchShape ls;
     ls.ok = false;
-    ls.fast = false;
+    ls.fast = 0;
     if (depth < 1) return ls;
+    if (shape == kBox2D && csize == 4 && nx % 4 == 0 && fast_box2d_supported(r, depth) &&
+        !std::getenv("SO2DR_GENERIC_KERNEL")) {
+        switch (r * 16 + depth) {
+            case 17: box_shape<1, 1>(ls, nx, esize); break;
+            case 18: box_shape<1, 2>(ls, nx, esize); break;
+            case 19: box_shape<1, 3>(ls, nx, esize); break;
+            case 20: box_shape<1, 4>(ls, nx, esize); break;
+            case 21: box_shape<1, 5>(ls, nx, esize); break;
+            case 22: box_shape<1, 6>(ls, nx, esize); break;
+            case 23: box_shape<1, 7>(ls, nx, esize); break;
+            case 24: box_shape<1, 8>(ls, nx, esize); break;
+            case 33: box_shape<2, 1>(ls, nx, esize); break;
+            case 34: box_shape<2, 2>(ls, nx, esize); break;
+            case 35: box_shape<2, 3>(ls, nx, esize); break;
+            case 36: box_shape<2, 4>(ls, nx, esize); break;
+            case 49: box_shape<3, 1>(ls, nx, esize); break;
+            case 50: box_shape<3, 2>(ls, nx, esize); break;
+            case 51: box_shape<3, 3>(ls, nx, esize); break;
+            case 65: box_shape<4, 1>(ls, nx, esize); break;
+            case 66: box_shape<4, 2>(ls, nx, esize); break;
+        }
+        if (ls.ok) return ls;
+    }
     if (shape == kStar3D && csize == 4 && nx % 4 == 0 && fast_star3d_supported(r, depth) &&
         !std::getenv("SO2DR_GENERIC_KERNEL")) {
         switch (r * 16 + depth) {

@@ -14,11 +14,16 @@ struct LaunchShape {
     size_t smem;
     int lx, ly, tx, ty;
     bool ok;
-    bool fast;   // register-streaming 3D star kernel (star3d_fast.cuh)
+    int fast;    // 0 generic kernel, kFastStar3D (star3d_fast.cuh), kFastBox2D (box2d_fast.cuh)
 };
+
+constexpr int kFastStar3D = 1, kFastBox2D = 2;
 
 // (R, K) pairs the register-streaming 3D star kernel is instantiated for.
 bool fast_star3d_supported(int r, int depth);
+
+// (R, K) pairs the register-streaming 2D box kernel is instantiated for.
+bool fast_box2d_supported(int r, int depth);
 
 // csize: compute-type bytes; esize: storage-type bytes.
 LaunchShape stencil_launch_shape(int shape, int r, int depth, int64_t ny, int64_t nx, int csize, int esize);

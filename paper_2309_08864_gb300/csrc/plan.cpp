@@ -538,6 +538,20 @@ void trapezoid_work(const Plan& p, double* computed, double* useful) {
 // included) of the kernels on one GB300: the register-streaming 3D star kernel
 // by radius and depth, and the generic kernel.
 double kernel_rate(const Plan& p, int depth) {
+    if (p.kind == SO2DR_BOX && p.ndim == 2 && p.dtype != SO2DR_F64 && p.nx % 4 == 0 && depth <= p.max_kon_auto) {
+        // 2D box kernel, in-core cell-steps/s measured on 16384^2 FP32
+        // (unmeasured depths interpolated)
+        static const double b1[9] = {0, 666e9, 864e9, 1000e9, 1125e9, 1180e9, 1230e9, 1260e9, 1288e9};
+        static const double b2[5] = {0, 455e9, 620e9, 690e9, 736e9};
+        static const double b3[4] = {0, 337e9, 350e9, 364e9};
+        static const double b4[3] = {0, 194e9, 222e9};
+        switch (p.r) {
+            case 1: return b1[std::min(depth, 8)];
+            case 2: return b2[std::min(depth, 4)];
+            case 3: return b3[std::min(depth, 3)];
+            default: return b4[std::min(depth, 2)];
+        }
+    }
     bool fast = p.kind == SO2DR_STAR && p.ndim == 3 && p.dtype != SO2DR_F64 && p.nx % 4 == 0 &&
                 depth <= p.max_kon_auto;
     if (!fast) return p.dtype == SO2DR_F64 ? 20e9 : 100e9;
@@ -557,8 +571,11 @@ double predict_ms(const Plan& p) {
     const double in_plane_bytes = (double)p.plane_bytes + (vc ? 6.0 * cells_plane * 4 : 0.0);
     const double host_h2d = (double)p.rounds * p.n0 * in_plane_bytes / (p.bw_h2d * 1e9);
     const double host_d2h = (double)p.rounds * p.interior_planes() * p.plane_bytes / (p.bw_d2h * 1e9);
-    // short out-of-core launches run at about 80% of the in-core rate
-    const double kernel = comp * cells_plane / (0.8 * kernel_rate(p, p.k_on));
+    // out-of-core launches lose a few planes' time each (axis-0 warm-up and
+    // the last wave of CTAs): about 80% of the in-core rate for chunks of ~45
+    // planes, nearly all of it for chunks of thousands of rows
+    const double pavg = (double)p.interior_planes() / std::max(1, p.d);
+    const double kernel = comp * cells_plane / (pavg / (pavg + 12.0) * kernel_rate(p, p.k_on));
     const int L = (int)launch_depths(p.k_off, p.k_on).size();
     const double units = (double)std::max(1, p.d * p.rounds);
     const double t_launch = kernel / (units * L), t_d2h_chunk = host_d2h / units;
@@ -741,7 +758,7 @@ int build_plan(Plan& p, int ndim, const int64_t* dims, int radius, int kind, con
             return fail(SO2DR_E_INFEASIBLE, "the adjoint rounds do not fit the device budget");
     }
     build_forward_in_core(p, p.ic);
-    if (p.kind == SO2DR_STAR && p.rounds > 0)
+    if (p.kind != SO2DR_VARCOEF_STAR && p.rounds > 0)
         if (!build_result_reuse(p, p.rr, p.budget, &p.rr_chunks)) p.rr_chunks = 0;
     int64_t cin, cx, cy, co;
     forward_caps(p, &cin, &cx, &cy, &co);

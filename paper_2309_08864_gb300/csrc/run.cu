@@ -362,6 +362,12 @@ int plan_create(so2dr_plan_t* out, int ndim, const int64_t* dims, int radius, in
                 if (fast_star3d_supported(radius, d)) fm = d;
             if (fm > 0) P->p.max_kon_auto = fm;
         }
+        if (shape == kBox2D && storage != SO2DR_F64 && ndim == 2 && dims && dims[1] % 4 == 0) {
+            int fm = 0;
+            for (int d = 1; d <= kMaxKon; ++d)
+                if (fast_box2d_supported(radius, d)) fm = d;
+            if (fm > 0) P->p.max_kon_auto = fm;
+        }
         rc = build_plan(P->p, ndim, dims, radius, kind, coeffs, ncoeffs, time_steps, min_chunks, k_on, k_off,
                         device_budget_bytes, storage, link_h2d_gbs, link_d2h_gbs, hbm_gbs, &err, search);
     } catch (const std::bad_alloc&) {

@@ -8,6 +8,7 @@ even), then float32 -> bfloat16 / float16 (round to nearest even).
 
 Seeds used by the workloads: 1 = initial field, 2 = target field,
 100 + f = face-coefficient field f, 7 = radius-4 coefficient table,
+11 + r = box2d{r}r coefficient table,
 1000 + k = finite-difference direction k.
 """
 import ctypes
@@ -120,6 +121,14 @@ def zero_ring(x: np.ndarray, r: int) -> np.ndarray:
         sl[a] = slice(x.shape[a] - r, x.shape[a])
         x[tuple(sl)] = 0
     return x
+
+
+def box2d_coeffs(r: int, seed: int = 11) -> np.ndarray:
+    """(2r+1)^2 independent draws in [0.5, 1.5) normalised in FP64 to sum to 1,
+    row-major from offset (-r, -r): the weights of the box2d{r}r workloads,
+    whose values the paper does not give."""
+    c = draw_box(seed + r, ((2 * r + 1) ** 2,), dist="uniform", a=0.5, b=1.5)
+    return c / c.sum()
 
 
 def radius4_star_coeffs(seed: int = 7, ndim: int = 3) -> np.ndarray:

@@ -103,6 +103,41 @@ def test_box2d_fp32(r):
     check_case((80, 301), r, "box", _coeffs(2, r, "box"), 9, so2dr.F32, 4, 4, 5, 0)
 
 
+@pytest.mark.parametrize("r,kon,koff,T,dtype", [
+    (1, 8, 16, 21, so2dr.F32),    # deepest launch, then a 5-step residual
+    (1, 4, 6, 13, so2dr.F32),
+    (2, 4, 8, 11, so2dr.F32),
+    (3, 3, 5, 11, so2dr.F32),
+    (4, 2, 4, 9, so2dr.F32),
+    (4, 1, 3, 5, so2dr.F32),
+    (1, 4, 8, 16, so2dr.BF16),
+    (2, 3, 6, 13, so2dr.F16),
+])
+def test_box2d_fast_kernel(r, kon, koff, T, dtype):
+    """Register-streaming 2D box kernel (the paper's box2d workloads, Table
+    III): three x tiles with a ragged last one, chunked rows, residual
+    launches, 16-bit storage."""
+    check_case((170, 2312), r, "box", _coeffs(2, r, "box"), T, dtype, 3, kon, koff, 0)
+
+
+@pytest.mark.parametrize("r,kon", [(1, 8), (2, 4), (3, 3), (4, 2)])
+def test_box2d_fast_kernel_matches_generic_kernel_bitwise(r, kon, monkeypatch):
+    """Both kernels sum each cell's products in the same order (row by row
+    from offset (-R, -R), a multiply first), so their FP32 results agree bit
+    for bit."""
+    import torch
+    dims, T = (96, 1104), kon + 1
+    st = inputs.to_storage(inputs.draw_box(3, dims), so2dr.F32)
+    plan = so2dr.Plan(dims, r, "box", _coeffs(2, r, "box"), T, k_on=kon, k_off=T, budget_bytes=0, dtype="f32")
+    fast = gu.pinned_from_storage(st.copy(), so2dr.F32)
+    plan.run(fast, in_core=True)
+    monkeypatch.setenv("SO2DR_GENERIC_KERNEL", "1")
+    generic = gu.pinned_from_storage(st.copy(), so2dr.F32)
+    plan.run(generic, in_core=True)
+    assert torch.equal(fast, generic)
+    assert not torch.equal(fast, gu.pinned_from_storage(st.copy(), so2dr.F32))
+
+
 @pytest.mark.parametrize("dtype", [so2dr.BF16, so2dr.F16])
 def test_star3d_16bit_storage(dtype):
     err, info, _, _ = check_case((64, 48, 52), 1, "star", [0.4] + [0.1] * 6, 16, dtype, 4, 4, 8, 0)

@@ -23,6 +23,7 @@ CASES = [
     ((40, 16), 1, "star", 10, 38, 4, 10, 0),    # one plane per chunk, P << 2rk
     ((33, 9, 11), 1, "varcoef", 7, 4, 2, 3, 0),
     ((512, 512), 1, "star", 16, 4, 4, 8, 1 << 20),  # the 2D Jacobi workload at full size
+    ((90, 40), 2, "box", 9, 3, 3, 4, 0),        # box stencil with chunks thick enough for result reuse
 ]
 
 
@@ -105,7 +106,8 @@ def test_buffer_options_stay_race_free(case, lookahead, nout, monkeypatch):
         assert np.array_equal(replay(p, u0, faces, policy=pol), ref)
 
 
-@pytest.mark.parametrize("case", [CASES[0], CASES[1], CASES[2], CASES[3], CASES[5], CASES[6], CASES[8], CASES[10]])
+@pytest.mark.parametrize("case", [CASES[0], CASES[1], CASES[2], CASES[3], CASES[5], CASES[6], CASES[8], CASES[10],
+                                  CASES[11]])
 def test_result_reuse_code_is_exact(case):
     """The redundancy-free comparison code (single-step launches, region
     sharing of intermediate results before every step) computes the same
