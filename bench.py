@@ -45,6 +45,9 @@ DRAM_PER_ALG_BYTE_R1K4_F32 = 1123.9 / 1073.7
 # (cudaMemcpyAsync, 4 GiB): host-to-device 211, device-to-host 193, both
 # directions at once 343 GB/s in total.
 LINK_H2D_GBS, LINK_D2H_GBS, LINK_BIDIR_GBS = 211.3, 193.4, 342.7
+# FP32 rate of the SM units (no tensor cores: a stencil is not a dense
+# contraction): 152 SMs x 128 FMA lanes x 2 FLOP x 2.07 GHz (maximum SM clock)
+ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
 CONFIGS = {
     # name: dims, radius, coefficients, steps, dtype, budget, min_chunks
@@ -531,6 +534,13 @@ def main():
     alg_bytes_per_launch = 2 * b * mk_cells / max(1, mk_n)
     avg_launch_s = mk_ms / max(1, mk_n) * 1e-3
     achieved = alg_bytes_per_launch / avg_launch_s / 1e9 if mk_n else 0.0
+    # FP32 work of the same launches: 2n - 1 FLOP per cell-step of an n-point
+    # stencil (Table III's count), against the FP32 rate of the SM units
+    npts = (2 * cfg["r"] + 1) ** 2 if cfg.get("kind") == "box" else 1 + 2 * cfg["r"] * len(cfg["dims"])
+    depth = info["k_on"] if mode != 2 else 1
+    alg_flops_per_launch = (2 * npts - 1) * depth * mk_cells / max(1, mk_n)
+    achieved_tf = alg_flops_per_launch / avg_launch_s / 1e12 if mk_n else 0.0
+    alu_bound = alg_flops_per_launch / (ALU_PEAK_TFLOPS * 1e12) > alg_bytes_per_launch / (hbm_peak * 1e9)
     # whole-path roofline: max(host-link time, HBM time) of the algorithmic bytes
     R, L = info["rounds"], -(-info["k_off"] // info["k_on"])
     Nb = 1
@@ -563,13 +573,20 @@ def main():
                           "measured_link_gbs": {"h2d": h2d / (stats[-1]["h2d_ms"] * 1e-3) / 1e9,
                                                 "d2h": d2h / (stats[-1]["d2h_ms"] * 1e-3) / 1e9,
                                                 "both_during_run": (h2d + d2h) / (stats[-1]["total_ms"] * 1e-3) / 1e9}},
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                     "frac": achieved / hbm_peak,
+        "roofline": {"bound": "alu" if alu_bound else "hbm",
+                     "achieved": achieved_tf if alu_bound else achieved,
+                     "peak": ALU_PEAK_TFLOPS if alu_bound else hbm_peak,
+                     "unit": "TFLOP/s" if alu_bound else "GB/s",
+                     "frac": achieved_tf / ALU_PEAK_TFLOPS if alu_bound else achieved / hbm_peak,
+                     "hbm": {"achieved_gbs": achieved, "peak_gbs": hbm_peak, "frac": achieved / hbm_peak},
+                     "alu": {"achieved_tflops": achieved_tf, "peak_tflops": ALU_PEAK_TFLOPS,
+                             "frac": achieved_tf / ALU_PEAK_TFLOPS, "flop_per_cell_step": 2 * npts - 1},
                      "traffic": (DRAM_PER_ALG_BYTE_R1K4_F32 * io_bytes / max(1, n_main)
                                  if (cfg.get("kind", "star"), len(cfg["dims"]), cfg["r"], info["k_on"],
                                      cfg["dtype"]) == ("star", 3, 1, 4, "f32") else None),
                      "kernel": ("box2d_fast_kernel" if cfg.get("kind") == "box" else "star3d_fast_kernel")
-                               + " (k_on-step TB launch)", "peak_kind": peak_kind + " (burst)",
+                               + " (k_on-step TB launch)", "peak_kind": ("derived from unit counts and the maximum SM clock" if alu_bound
+                                   else peak_kind + " (burst)"),
                      "avg_launch_ms": avg_launch_s * 1e3, "launches": mk_n},
         "e2e": {"value": e2e, "unit": "Gcell/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": int(sum(s["launches"] for s in stats)),

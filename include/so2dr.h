@@ -117,7 +117,8 @@ typedef struct {
 /* Filled by so2dr_run / so2dr_adjoint when the caller passes a non-NULL pointer. */
 typedef struct {
     double total_ms;     /* first enqueue to last completion, CUDA events          */
-    double kernel_ms;    /* sum of kernel durations (event pairs per launch)       */
+    double kernel_ms;    /* sum of kernel durations (event pairs per launch; in
+                            mode 2 also the on-device region-sharing copies)     */
     double h2d_ms;       /* sum of host-to-device copy durations                   */
     double d2h_ms;       /* sum of device-to-host copy durations                   */
     double h2d_bytes;
@@ -125,7 +126,8 @@ typedef struct {
     int64_t launches;
     int64_t ops;
     double gcells_per_s; /* cell_updates / total_ms                                */
-    double main_kernel_ms;      /* sum of durations of the k_on-deep launches       */
+    double main_kernel_ms;      /* sum of durations of the k_on-deep launches (depth
+                                   1 in the result-reuse code, mode 2)              */
     int64_t main_kernel_launches;
     double main_kernel_cells;   /* owned (useful) cells those launches produced     */
 } so2dr_stats_t;

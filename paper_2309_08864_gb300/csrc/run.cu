@@ -318,10 +318,13 @@ int execute(so2dr_plan_s* P, const RunList& rl, char* const* hosts, const int64_
             else if (o.kind == kOpD2H) stats->d2h_ms += d;
             else {
                 stats->kernel_ms += d;
-                if (o.depth == P->p.k_on && rl.ops[j].fn == kFnStencil) {
-                    // algorithmic cells: the chunk's owned planes (the whole grid in-core)
-                    const Plan& pp = P->p;
-                    int64_t owned = (&rl == &pp.ooc) ? pp.starts[o.chunk + 1] - pp.starts[o.chunk] : pp.n0;
+                const Plan& pp = P->p;
+                const bool rr = &rl == &pp.rr;  // the result-reuse code runs depth-1 launches only
+                if (o.depth == (rr ? 1 : pp.k_on) && rl.ops[j].fn == kFnStencil) {
+                    // algorithmic cells: the chunk's owned planes (the whole grid in-core;
+                    // the launch's own output planes in the result-reuse code)
+                    int64_t owned = (&rl == &pp.ooc) ? pp.starts[o.chunk + 1] - pp.starts[o.chunk]
+                                                     : rr ? o.dst_hi - o.dst_lo : pp.n0;
                     stats->main_kernel_ms += d;
                     stats->main_kernel_launches += 1;
                     stats->main_kernel_cells += (double)owned * (double)pp.plane_cells;
