@@ -148,7 +148,7 @@ int choose_segments(int64_t tiles, int64_t nout, int r, int depth, int sms, int 
     int64_t slots = (int64_t)sms * (occ > 0 ? occ : 1);
     int best = 1;
     double best_cost = 0;
-    for (int n = 1; n <= 16 && n <= nout; ++n) {
+    for (int n = 1; n <= 64 && n <= nout; ++n) {
         int64_t waves = (tiles * n + slots - 1) / slots;
         double len = (double)nout / n + 2.0 * r * depth + depth;  // planes one CTA streams
         double cost = (double)waves * len;
