@@ -448,6 +448,9 @@ def main():
     ap.add_argument("--sweep", default="",
                     help="comma-separated k_off values: measured and predicted time of one run per k_off "
                          "(the run-time tuning trade-off of Sec. V-B); prints one JSON line")
+    ap.add_argument("--link", action="store_true",
+                    help="measure the host link (copy engines vs SM-driven copies over the mapped pinned "
+                         "buffers, each direction and both at once) and HBM; prints one JSON line")
     args = ap.parse_args()
     cfg = dict(CONFIGS[args.config])
     if args.k_off is not None:
@@ -463,6 +466,13 @@ def main():
     torch.cuda.set_device(local)
     if args.kernel_case:
         return run_kernel_case(args)
+    if args.link:
+        rows = {}
+        for ctas in (32, 64, 152):
+            rows[ctas] = so2dr.measure_link(1 << 30, sm_ctas=ctas, repeats=3)
+        print(json.dumps({"link_gbs": rows, "bytes": 1 << 30, "note": "keys by SM-copy CTA count; ce_* are "
+                          "cudaMemcpyAsync, sm_* a copy kernel over the mapped pinned buffer"}), flush=True)
+        return 0
     if cfg.get("adjoint"):
         return run_adjoint(args, cfg, world, rank, local)
 

@@ -312,6 +312,27 @@ int so2dr_autotune(int ndim, const int64_t* dims, int radius, int kind, const do
                    int* table_len, double* link_gbs);
 
 /*
+ * Host-link and HBM rates on the caller's buffers, in GB/s: the rates the
+ * cost model of Sec. III balances, and the comparison of the copy engines
+ * with SM-driven transfers over the mapped pinned buffer (on GB300 the
+ * Grace-Blackwell C2C link; the zero-copy alternative to cudaMemcpyAsync).
+ *   host_a, host_b  pinned host buffers of `bytes` each (contents overwritten).
+ *   device_arena    device memory of 2 * bytes.
+ *   bytes           transfer size, a multiple of 16, >= 1 MiB.
+ *   sm_ctas         CTAs of the SM copy kernel (e.g. 64).
+ *   repeats         timed transfers per figure (the best is kept), >= 1.
+ *   out             9 rates: [0] copy-engine host-to-device, [1] copy-engine
+ *                   device-to-host, [2] and [3] the same two at once (two
+ *                   streams), [4] SM host-to-device, [5] SM device-to-host,
+ *                   [6] and [7] the two SM directions at once, [8] HBM (an
+ *                   on-device copy, read + write bytes).  SM figures are -1
+ *                   when the host buffers have no device mapping.
+ * Synchronises the device work it issues; uses its own streams.
+ */
+int so2dr_measure_link(void* host_a, void* host_b, void* device_arena, size_t bytes, int sm_ctas,
+                       int repeats, double* out);
+
+/*
  * Gradient of L = 1/2 ||u_T - u*||^2 (T = time_steps) for a VARCOEF_STAR plan,
  * through the same out-of-core pipeline: a forward sweep that keeps u every
  * checkpoint_every steps in host_workspace, then, segment by segment from the

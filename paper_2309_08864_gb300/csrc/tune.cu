@@ -1,11 +1,12 @@
 // tune.cu -- the run-time parameter search of Sec. IV-C: the cost model's
 // ranked candidate list, plans built from one candidate, and the measured
 // autotune that times the best candidates on the device (the trade-off that
-// Sec. V-B's Fig. 5 measures).
+// Sec. V-B's Fig. 5 measures), and the host-link / HBM measurement they use.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cstring>
+#include <initializer_list>
 #include <vector>
 
 #include "run.hpp"
@@ -104,6 +105,61 @@ int time_copy(void* dst, const void* src, size_t bytes, cudaMemcpyKind kind, cud
 
 bool fatal(int rc) { return rc == SO2DR_E_CUDA || rc == SO2DR_E_TIMEOUT || rc == SO2DR_E_DEVICE_CHECK; }
 
+// SM-driven copy of n 16-byte vectors (grid-stride, 4 vectors in flight per
+// thread); either side may be mapped host memory
+__global__ void __launch_bounds__(512) link_copy_kernel(const int4* __restrict__ src, int4* __restrict__ dst,
+                                                        size_t n) {
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (; i + 3 * stride < n; i += 4 * stride) {
+        const int4 a = src[i], b = src[i + stride], c = src[i + 2 * stride], d = src[i + 3 * stride];
+        dst[i] = a;
+        dst[i + stride] = b;
+        dst[i + 2 * stride] = c;
+        dst[i + 3 * stride] = d;
+    }
+    for (; i < n; i += stride) dst[i] = src[i];
+}
+
+struct Xfer {
+    void* dst;
+    const void* src;
+    cudaMemcpyKind kind;  // copy engine, or cudaMemcpyDefault for the SM kernel
+};
+
+// Runs one or two transfers at once (one stream each), `reps` times; best
+// GB/s of each in gbs[] (0 on no timing).
+int time_xfers(const Xfer* x, int nx, size_t bytes, int ctas, int reps, cudaStream_t* st, cudaEvent_t* ev,
+               double* gbs) {
+    for (int k = 0; k < nx; ++k) gbs[k] = 0;
+    for (int r = 0; r < reps; ++r) {
+        for (int k = 0; k < nx; ++k) {
+            cudaError_t e = cudaEventRecord(ev[2 * k], st[k]);
+            if (e == cudaSuccess) {
+                if (x[k].kind == cudaMemcpyDefault) {
+                    link_copy_kernel<<<ctas, 512, 0, st[k]>>>(static_cast<const int4*>(x[k].src),
+                                                              static_cast<int4*>(x[k].dst), bytes / 16);
+                    e = cudaGetLastError();
+                } else {
+                    e = cudaMemcpyAsync(x[k].dst, x[k].src, bytes, x[k].kind, st[k]);
+                }
+            }
+            if (e == cudaSuccess) e = cudaEventRecord(ev[2 * k + 1], st[k]);
+            if (e != cudaSuccess) return cuda_fail(e, "link measurement");
+        }
+        std::vector<cudaEvent_t> ends;
+        for (int k = 0; k < nx; ++k) ends.push_back(ev[2 * k + 1]);
+        int rc = bounded_wait(ends, wait_timeout_s());
+        if (rc) return rc;
+        for (int k = 0; k < nx; ++k) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, ev[2 * k], ev[2 * k + 1]) == cudaSuccess && ms > 0.f)
+                gbs[k] = std::max(gbs[k], bytes / (ms * 1e-3) / 1e9);
+        }
+    }
+    return SO2DR_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -133,6 +189,51 @@ int so2dr_plan_tuned(so2dr_plan_t* out, int ndim, const int64_t* dims, int radiu
     if (!entry) return set_error(SO2DR_E_INVAL, "entry is NULL");
     Problem q{ndim, dims, radius, kind, coeffs, ncoeffs, time_steps, 1, 0, 0, device_budget_bytes, storage};
     return plan_for(q, *entry, 0, 0, 0, out);
+}
+
+int so2dr_measure_link(void* host_a, void* host_b, void* device_arena, size_t bytes, int sm_ctas, int repeats,
+                       double* out) {
+    if (!host_a || !host_b || !device_arena || !out) return set_error(SO2DR_E_INVAL, "NULL argument");
+    if (bytes < ((size_t)1 << 20) || bytes % 16) return set_error(SO2DR_E_INVAL, "bytes must be >= 1 MiB and a multiple of 16");
+    if (sm_ctas < 1 || repeats < 1) return set_error(SO2DR_E_INVAL, "sm_ctas and repeats must be >= 1");
+    int rc = check_pinned(host_a, "host_a");
+    if (rc == SO2DR_OK) rc = check_pinned(host_b, "host_b");
+    if (rc) return rc;
+    for (int k = 0; k < 9; ++k) out[k] = -1.0;
+    void *ma = nullptr, *mb = nullptr;  // device views of the pinned buffers
+    const bool mapped = cudaHostGetDevicePointer(&ma, host_a, 0) == cudaSuccess &&
+                        cudaHostGetDevicePointer(&mb, host_b, 0) == cudaSuccess;
+    if (!mapped) cudaGetLastError();
+    char* d0 = static_cast<char*>(device_arena);
+    char* d1 = d0 + bytes;
+    cudaStream_t st[2] = {nullptr, nullptr};
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = cudaStreamCreateWithFlags(&st[k], cudaStreamNonBlocking);
+    for (int k = 0; k < 4 && e == cudaSuccess; ++k) e = cudaEventCreate(&ev[k]);
+    if (e != cudaSuccess) rc = cuda_fail(e, "stream or event creation");
+    double g[2];
+    auto run = [&](std::initializer_list<Xfer> xs, int o0) {
+        if (rc) return;
+        std::vector<Xfer> v(xs);
+        rc = time_xfers(v.data(), (int)v.size(), bytes, sm_ctas, repeats, st, ev, g);
+        for (size_t k = 0; k < v.size() && rc == SO2DR_OK; ++k) out[o0 + k] = g[k];
+    };
+    run({{d0, host_a, cudaMemcpyHostToDevice}}, 0);
+    run({{host_b, d1, cudaMemcpyDeviceToHost}}, 1);
+    run({{d0, host_a, cudaMemcpyHostToDevice}, {host_b, d1, cudaMemcpyDeviceToHost}}, 2);
+    if (mapped) {
+        run({{d0, ma, cudaMemcpyDefault}}, 4);
+        run({{mb, d1, cudaMemcpyDefault}}, 5);
+        run({{d0, ma, cudaMemcpyDefault}, {mb, d1, cudaMemcpyDefault}}, 6);
+    }
+    run({{d1, d0, cudaMemcpyDeviceToDevice}}, 8);
+    if (rc == SO2DR_OK && out[8] > 0) out[8] *= 2.0;  // read + write
+    for (int k = 0; k < 4; ++k)
+        if (ev[k]) cudaEventDestroy(ev[k]);
+    for (int k = 0; k < 2; ++k)
+        if (st[k]) cudaStreamDestroy(st[k]);
+    return rc;
 }
 
 int so2dr_autotune(int ndim, const int64_t* dims, int radius, int kind, const double* coeffs, int ncoeffs,

@@ -23,7 +23,8 @@ OK, E_INVAL, E_INFEASIBLE, E_NOT_BOUND, E_CUDA, E_TIMEOUT, E_DEVICE_CHECK, E_NOM
 SYMBOLS = ["so2dr_plan", "so2dr_plan_ex", "so2dr_plan_info", "so2dr_plan_chunks", "so2dr_plan_ops",
            "so2dr_plan_buffers", "so2dr_bind", "so2dr_run", "so2dr_adjoint", "so2dr_loss", "so2dr_dot",
            "so2dr_destroy", "so2dr_strerror", "so2dr_last_error", "so2dr_abi_version",
-           "so2dr_run_device_noalloc", "so2dr_plan_candidates", "so2dr_plan_tuned", "so2dr_autotune"]
+           "so2dr_run_device_noalloc", "so2dr_plan_candidates", "so2dr_plan_tuned", "so2dr_autotune",
+           "so2dr_measure_link"]
 
 
 class So2drError(RuntimeError):
@@ -116,6 +117,7 @@ def load_library(path=None):
     lib.so2dr_autotune.argtypes = [c_int, i64p, c_int, c_int, dp, c_int, i64, c_int, c_int, c_int, c_size,
                                    c_int, vp, ctypes.POINTER(vp), c_int, vp, c_int, c_int, tep, c_int,
                                    ctypes.POINTER(c_int), dp]
+    lib.so2dr_measure_link.argtypes = [vp, vp, vp, c_size, c_int, c_int, dp]
     lib.so2dr_destroy.argtypes = [vp]
     lib.so2dr_destroy.restype = None
     lib.so2dr_strerror.argtypes = [c_int]
@@ -363,6 +365,25 @@ def autotune(dims, radius=1, kind="star", coeffs=None, time_steps=1, budget_byte
                               len(streams), _ptr(scratch), int(max_candidates), int(repeats), arr, cap,
                               ctypes.byref(n), link))
     return [{k: getattr(e, k) for k, _ in TuneEntry._fields_} for e in arr[:min(cap, n.value)]], tuple(link)
+
+
+LINK_KEYS = ("ce_h2d", "ce_d2h", "ce_both_h2d", "ce_both_d2h", "sm_h2d", "sm_d2h", "sm_both_h2d", "sm_both_d2h",
+             "hbm")
+
+
+def measure_link(bytes_=1 << 30, sm_ctas=64, repeats=3):
+    """Host-link and HBM rates in GB/s (so2dr_measure_link): copy engines and
+    SM-driven copies over the mapped pinned buffers, each direction alone and
+    both at once, and an on-device copy."""
+    import torch
+    lib = load_library()
+    a = torch.empty(int(bytes_), dtype=torch.uint8).pin_memory()
+    b = torch.empty(int(bytes_), dtype=torch.uint8).pin_memory()
+    arena = torch.empty(2 * int(bytes_), dtype=torch.uint8, device="cuda")
+    out = (ctypes.c_double * 9)()
+    _check(lib.so2dr_measure_link(_ptr(a), _ptr(b), ctypes.c_void_p(arena.data_ptr()), int(bytes_), int(sm_ctas),
+                                  int(repeats), out))
+    return dict(zip(LINK_KEYS, list(out)))
 
 
 def _varcoef_loss_fn():

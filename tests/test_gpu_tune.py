@@ -46,3 +46,12 @@ def test_autotune_ranks_measured_candidates_and_the_winner_is_exact(dims, T, bud
     ref = oracle.run(inputs.storage_to_f64(st, dtype), gu.compute_coeffs(C7, dtype), 1, 0, T)
     err = gu.rel_linf(gu.storage_of(ooc, dtype), ref)
     assert err <= (1e-5 if dtype == so2dr.F32 else 2e-2), err
+
+
+def test_measure_link_reports_every_rate():
+    r = so2dr.measure_link(64 << 20, sm_ctas=64, repeats=2)
+    assert set(r) == set(so2dr.LINK_KEYS)
+    for k, v in r.items():
+        assert v > 1.0, (k, v)   # GB/s; pinned buffers from torch are mapped on this platform
+    assert r["hbm"] > r["ce_h2d"]
+

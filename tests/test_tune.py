@@ -68,3 +68,15 @@ def test_bad_entries_are_rejected():
     with pytest.raises(so2dr.So2drError) as ex:
         so2dr.candidates(**dict(prob, budget_bytes=4096))
     assert ex.value.code == so2dr.E_INFEASIBLE
+
+
+def test_measure_link_rejects_bad_arguments_before_any_device_work():
+    lib = so2dr.load_library()
+    import ctypes
+    out = (ctypes.c_double * 9)()
+    buf = ctypes.create_string_buffer(16)
+    assert lib.so2dr_measure_link(None, None, None, 1 << 20, 64, 1, out) == so2dr.E_INVAL
+    assert lib.so2dr_measure_link(buf, buf, buf, 1000, 64, 1, out) == so2dr.E_INVAL   # < 1 MiB
+    assert lib.so2dr_measure_link(buf, buf, buf, (1 << 20) + 8, 64, 1, out) == so2dr.E_INVAL  # not 16-byte multiple
+    assert lib.so2dr_measure_link(buf, buf, buf, 1 << 20, 0, 1, out) == so2dr.E_INVAL
+
