@@ -37,10 +37,10 @@ sys.path.insert(0, ROOT)
 MEASURED = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # DRAM bytes per algorithmic byte of star3d_fast_kernel<float, 1, 4>, from the
 # full ncu capture of a 512^3 in-core launch (dram__bytes_read.sum +
-# dram__bytes_write.sum = 607.08 + 494.52 MB for 1073.74 MB of algorithmic
+# dram__bytes_write.sum = 579.49 + 493.90 MB for 1073.74 MB of algorithmic
 # reads and writes); traffic grows with the planes a launch streams, so a
 # launch's traffic is this ratio times its (input + output) plane bytes.
-DRAM_PER_ALG_BYTE_R1K4_F32 = (607.08 + 494.52) / 1073.74
+DRAM_PER_ALG_BYTE_R1K4_F32 = (579.49 + 493.90) / 1073.74
 # host-link bandwidths measured on the GB300 machines with pinned buffers
 # (cudaMemcpyAsync, 4 GiB): host-to-device 211, device-to-host 193, both
 # directions at once 343 GB/s in total.

@@ -57,7 +57,7 @@ def build(force: bool = False, verbose: bool = False, checked: bool = False) -> 
     common = ["-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC]
     if checked:
         common.append("-DSO2DR_CHECKED=1")
-    # extra flags for experiments (e.g. -DSO2DR_K4_VY4=1); part of the build stamp
+    # extra nvcc flags from SO2DR_NVCC_FLAGS (part of the build stamp)
     common += os.environ.get("SO2DR_NVCC_FLAGS", "").split()
     cu_flags = common + ARCH + ["-lineinfo", "-fmad=true", "--expt-relaxed-constexpr"]
     jobs = []

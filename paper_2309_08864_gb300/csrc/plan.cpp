@@ -556,7 +556,7 @@ double kernel_rate(const Plan& p, int depth) {
                 depth <= p.max_kon_auto;
     if (!fast) return p.dtype == SO2DR_F64 ? 20e9 : 100e9;
     if (p.r == 1) {
-        const double r1[5] = {0, 512e9, 750e9, 990e9, 970e9};
+        const double r1[5] = {0, 512e9, 750e9, 990e9, 990e9};
         return r1[std::min(depth, 4)];
     }
     if (p.r == 2) return depth >= 2 ? 450e9 : 380e9;
