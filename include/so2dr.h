@@ -175,7 +175,9 @@ typedef struct {
  *                  buffer fits device_budget_bytes (so2dr_plan_info reports
  *                  the chosen d).
  *   k_on           steps fused per launch (1..16), 0 = choose.
- *   k_off          steps per round (>= 1), 0 = choose from the cost model.
+ *   k_off          steps per round (>= 1), 0 = choose from the cost model
+ *                  (among the candidates predicted within 2% of the best, the
+ *                  one with the fewest rounds; see so2dr_plan_candidates).
  *   device_budget_bytes  every device byte the out-of-core pipeline uses.
  *   storage        grid storage dtype.
  * Returns SO2DR_E_INFEASIBLE when no chunking fits the budget.

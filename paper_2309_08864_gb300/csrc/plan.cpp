@@ -571,11 +571,13 @@ double predict_ms(const Plan& p) {
     const double in_plane_bytes = (double)p.plane_bytes + (vc ? 6.0 * cells_plane * 4 : 0.0);
     const double host_h2d = (double)p.rounds * p.n0 * in_plane_bytes / (p.bw_h2d * 1e9);
     const double host_d2h = (double)p.rounds * p.interior_planes() * p.plane_bytes / (p.bw_d2h * 1e9);
-    // out-of-core launches lose a few planes' time each (axis-0 warm-up and
-    // the last wave of CTAs): about 80% of the in-core rate for chunks of ~45
-    // planes, nearly all of it for chunks of thousands of rows
+    // out-of-core launches run at about 80% of the in-core rate for chunks of
+    // 20-60 planes (measured: 0.77-0.82, the second compute stream filling
+    // part of each launch's last wave), and at nearly all of it for chunks of
+    // thousands of rows
     const double pavg = (double)p.interior_planes() / std::max(1, p.d);
-    const double kernel = comp * cells_plane / (pavg / (pavg + 12.0) * kernel_rate(p, p.k_on));
+    const double eff = std::max(0.8, pavg / (pavg + 12.0));
+    const double kernel = comp * cells_plane / (eff * kernel_rate(p, p.k_on));
     const int L = (int)launch_depths(p.k_off, p.k_on).size();
     const double units = (double)std::max(1, p.d * p.rounds);
     const double t_launch = kernel / (units * L), t_d2h_chunk = host_d2h / units;
@@ -701,6 +703,7 @@ int build_plan(Plan& p, int ndim, const int64_t* dims, int radius, int kind, con
         }
         double best = std::numeric_limits<double>::infinity();
         int bko = 0, bkn = 0, bd = 0, bla = 1, bno = 2;
+        std::vector<Candidate> feasible;
         // buffer options (look-ahead, output slabs); SO2DR_LOOKAHEAD / SO2DR_NOUT pin one
         const char* ela = std::getenv("SO2DR_LOOKAHEAD");
         const char* eno = std::getenv("SO2DR_NOUT");
@@ -724,18 +727,36 @@ int build_plan(Plan& p, int ndim, const int64_t* dims, int radius, int kind, con
                     int d = fit_chunks(q, min_chunks);
                     if (!d) continue;
                     double ms = predict_ms(q);
-                    if (search && search->ranked) {
-                        Candidate c;
-                        c.k_off = q.k_off;
-                        c.k_on = q.k_on;
-                        c.d = d;
-                        c.lookahead = la;
-                        c.n_out = no;
-                        c.predicted_ms = ms;
-                        search->ranked->push_back(c);
-                    }
-                    if (ms < best) { best = ms; bko = q.k_off; bkn = q.k_on; bd = d; bla = la; bno = no; }
+                    Candidate c;
+                    c.k_off = q.k_off;
+                    c.k_on = q.k_on;
+                    c.d = d;
+                    c.lookahead = la;
+                    c.n_out = no;
+                    c.predicted_ms = ms;
+                    feasible.push_back(c);
+                    if (search && search->ranked) search->ranked->push_back(c);
+                    if (ms < best) best = ms;
                 }
+            }
+        }
+        // Among the candidates predicted within 2% of the best, take the one
+        // with the fewest rounds (least host-link traffic), then the lowest
+        // prediction: the model cannot tell them apart, and the host link,
+        // shared with the rest of the host, is the most variable resource.
+        int brounds = std::numeric_limits<int>::max();
+        double bms = std::numeric_limits<double>::infinity();
+        for (const Candidate& c : feasible) {
+            if (c.predicted_ms > 1.02 * best) continue;
+            const int rounds = (int)((T + c.k_off - 1) / c.k_off);
+            if (rounds < brounds || (rounds == brounds && c.predicted_ms < bms)) {
+                brounds = rounds;
+                bms = c.predicted_ms;
+                bko = c.k_off;
+                bkn = c.k_on;
+                bd = c.d;
+                bla = c.lookahead;
+                bno = c.n_out;
             }
         }
         if (!bd) return fail(SO2DR_E_INFEASIBLE, "no chunking fits the device budget");
