@@ -448,6 +448,8 @@ def main():
     ap.add_argument("--sweep", default="",
                     help="comma-separated k_off values: measured and predicted time of one run per k_off "
                          "(the run-time tuning trade-off of Sec. V-B); prints one JSON line")
+    ap.add_argument("--timeline", default="",
+                    help="write the per-op timeline (so2dr_run_timeline) of the last timed run to this JSON file")
     ap.add_argument("--link", action="store_true",
                     help="measure the host link (copy engines vs SM-driven copies over the mapped pinned "
                          "buffers, each direction and both at once) and HBM; prints one JSON line")
@@ -607,6 +609,9 @@ def main():
     }
     if tuned:
         line["autotune"] = tuned
+    if args.timeline:
+        with open(args.timeline, "w") as f:
+            json.dump(plan.timeline(in_core=mode), f)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         from paper_2309_08864_gb300 import inputs as _inp
         import oracle

@@ -290,6 +290,16 @@ int so2dr_run(so2dr_plan_t plan, void* host_grid, const void* host_coeff_fields,
               so2dr_stats_t* stats);
 
 /*
+ * Timeline of the last run made with stats (tracing): for op j of the list
+ * that run replayed (the order of so2dr_plan_ops for its mode; for
+ * so2dr_adjoint and so2dr_loss, the last of their pipelines), the time its
+ * stream reached it after its waits and the time it completed, in ms from the
+ * run's start marker (CUDA events).  With both arrays NULL only *n_ops is
+ * set; 0 ops before any timed run.
+ */
+int so2dr_run_timeline(so2dr_plan_t plan, double* start_ms, double* end_ms, int64_t max_ops, int64_t* n_ops);
+
+/*
  * Measured autotune of the run-time parameters (Sec. IV-C's choice of d,
  * k_off and k_on, made by timing instead of by the model alone).
  *   1. Measures the host link (host-to-device and device-to-host copies of

@@ -310,9 +310,15 @@ int execute(so2dr_plan_s* P, const RunList& rl, char* const* hosts, const int64_
         std::memset(stats, 0, sizeof(*stats));
         cudaEventElapsedTime(&ms, tstart, tend);
         stats->total_ms = ms;
+        P->tl_start.assign(nops, 0.0);
+        P->tl_end.assign(nops, 0.0);
         for (size_t j = 0; j < nops; ++j) {
-            float d = 0;
+            float d = 0, t0 = 0, t1 = 0;
             cudaEventElapsedTime(&d, P->tev[2 * j], P->tev[2 * j + 1]);
+            cudaEventElapsedTime(&t0, tstart, P->tev[2 * j]);
+            cudaEventElapsedTime(&t1, tstart, P->tev[2 * j + 1]);
+            P->tl_start[j] = t0;
+            P->tl_end[j] = t1;
             const so2dr_op_t& o = rl.ops[j].pub;
             if (o.kind == kOpH2D) stats->h2d_ms += d;
             else if (o.kind == kOpD2H) stats->d2h_ms += d;
@@ -472,6 +478,19 @@ int so2dr_plan_info(so2dr_plan_t P, so2dr_plan_info_t* info) {
     info->out_slabs = p.n_out;
     info->arena_bytes_result_reuse = p.rr_chunks ? p.rr.arena_bytes : 0;
     info->result_reuse_chunks = p.rr_chunks;
+    return SO2DR_OK;
+}
+
+int so2dr_run_timeline(so2dr_plan_t P, double* start_ms, double* end_ms, int64_t max_ops, int64_t* n_ops) {
+    if (!P || !n_ops) return set_error(SO2DR_E_INVAL, "NULL argument");
+    *n_ops = (int64_t)P->tl_start.size();
+    if (!start_ms && !end_ms) return SO2DR_OK;
+    if (!start_ms || !end_ms) return set_error(SO2DR_E_INVAL, "start_ms and end_ms must both be given");
+    if (max_ops < *n_ops) return set_error(SO2DR_E_INVAL, "arrays too small");
+    for (int64_t j = 0; j < *n_ops; ++j) {
+        start_ms[j] = P->tl_start[(size_t)j];
+        end_ms[j] = P->tl_end[(size_t)j];
+    }
     return SO2DR_OK;
 }
 

@@ -24,7 +24,7 @@ SYMBOLS = ["so2dr_plan", "so2dr_plan_ex", "so2dr_plan_info", "so2dr_plan_chunks"
            "so2dr_plan_buffers", "so2dr_bind", "so2dr_run", "so2dr_adjoint", "so2dr_loss", "so2dr_dot",
            "so2dr_destroy", "so2dr_strerror", "so2dr_last_error", "so2dr_abi_version",
            "so2dr_run_device_noalloc", "so2dr_plan_candidates", "so2dr_plan_tuned", "so2dr_autotune",
-           "so2dr_measure_link"]
+           "so2dr_measure_link", "so2dr_run_timeline"]
 
 
 class So2drError(RuntimeError):
@@ -118,6 +118,7 @@ def load_library(path=None):
                                    c_int, vp, ctypes.POINTER(vp), c_int, vp, c_int, c_int, tep, c_int,
                                    ctypes.POINTER(c_int), dp]
     lib.so2dr_measure_link.argtypes = [vp, vp, vp, c_size, c_int, c_int, dp]
+    lib.so2dr_run_timeline.argtypes = [vp, dp, dp, i64, i64p]
     lib.so2dr_destroy.argtypes = [vp]
     lib.so2dr_destroy.restype = None
     lib.so2dr_strerror.argtypes = [c_int]
@@ -269,6 +270,20 @@ class Plan:
         _check(load_library().so2dr_run(self._h, _ptr(host_grid), _ptr(coeff_fields), int(in_core),
                                          ctypes.byref(st) if stats else None))
         return _stats_dict(st) if stats else None
+
+    def timeline(self, in_core=False):
+        """Per-op (start_ms, end_ms) of the last run made with stats, joined
+        with the op records of that mode (so2dr_run_timeline)."""
+        lib = load_library()
+        n = ctypes.c_int64()
+        _check(lib.so2dr_run_timeline(self._h, None, None, 0, ctypes.byref(n)))
+        a = (ctypes.c_double * max(1, n.value))()
+        b = (ctypes.c_double * max(1, n.value))()
+        _check(lib.so2dr_run_timeline(self._h, a, b, n.value, ctypes.byref(n)))
+        ops = self.ops(in_core)
+        if len(ops) != n.value:
+            raise So2drError(E_INVAL, "the last timed run replayed another op list")
+        return [dict(o, start_ms=a[j], end_ms=b[j]) for j, o in enumerate(ops)]
 
     def adjoint(self, u0, coeff_fields, target, grad_u0, grad_coeffs, workspace, checkpoint_every=8,
                 stats=True):
