@@ -162,6 +162,21 @@ typedef struct {
     int64_t capacity_planes;
 } so2dr_buffer_t;
 
+/*
+ * Environment variables the library reads:
+ *   SO2DR_TIMEOUT_S       limit of every bounded wait on the device, seconds
+ *                         (default 600); past it a call returns
+ *                         SO2DR_E_TIMEOUT instead of waiting on.
+ *   SO2DR_LOOKAHEAD=0|1   pin the planner's look-ahead option (default: the
+ *   SO2DR_NOUT=1|2        cost model chooses); likewise the output slabs.
+ *   SO2DR_GENERIC_KERNEL  any value: launch the generic temporal-blocking
+ *                         kernel even where a register-streaming one exists
+ *                         (same per-cell summation order, same results).
+ *   SO2DR_ALLOW_PAGEABLE  any value: skip the page-locked check on host
+ *                         grids (copies from pageable memory are staged by
+ *                         the driver and run slower).
+ */
+
 /* ---------------------------------------------------------------- planning */
 
 /*

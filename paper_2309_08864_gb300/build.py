@@ -45,9 +45,9 @@ def _digest():
     return h.hexdigest()[:16]
 
 
-def build(force: bool = False, verbose: bool = False, checked: bool = False) -> str:
+def build(force: bool = False, verbose: bool = False) -> str:
     stamp = os.path.join(BUILD_DIR, "stamp")
-    dig = _digest() + ("-checked" if checked else "")
+    dig = _digest()
     if not force and os.path.exists(LIB) and os.path.exists(stamp):
         with open(stamp) as f:
             if f.read().strip() == dig:
@@ -55,8 +55,6 @@ def build(force: bool = False, verbose: bool = False, checked: bool = False) -> 
     os.makedirs(BUILD_DIR, exist_ok=True)
     nvcc = _nvcc()
     common = ["-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC]
-    if checked:
-        common.append("-DSO2DR_CHECKED=1")
     # extra nvcc flags from SO2DR_NVCC_FLAGS (part of the build stamp)
     common += os.environ.get("SO2DR_NVCC_FLAGS", "").split()
     cu_flags = common + ARCH + ["-lineinfo", "-fmad=true", "--expt-relaxed-constexpr"]
@@ -92,4 +90,4 @@ def build(force: bool = False, verbose: bool = False, checked: bool = False) -> 
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose=True, checked="--checked" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose=True))
