@@ -541,10 +541,10 @@ double kernel_rate(const Plan& p, int depth) {
     if (p.kind == SO2DR_BOX && p.ndim == 2 && p.dtype != SO2DR_F64 && p.nx % 4 == 0 && depth <= p.max_kon_auto) {
         // 2D box kernel, in-core cell-steps/s measured on 16384^2 FP32
         // (unmeasured depths interpolated)
-        static const double b1[9] = {0, 666e9, 864e9, 1000e9, 1125e9, 1180e9, 1230e9, 1260e9, 1288e9};
-        static const double b2[5] = {0, 455e9, 620e9, 690e9, 736e9};
-        static const double b3[4] = {0, 337e9, 350e9, 364e9};
-        static const double b4[3] = {0, 194e9, 222e9};
+        static const double b1[9] = {0, 757e9, 1029e9, 1120e9, 1203e9, 1250e9, 1300e9, 1340e9, 1368e9};
+        static const double b2[5] = {0, 557e9, 703e9, 745e9, 786e9};
+        static const double b3[4] = {0, 371e9, 375e9, 384e9};
+        static const double b4[3] = {0, 248e9, 238e9};
         switch (p.r) {
             case 1: return b1[std::min(depth, 8)];
             case 2: return b2[std::min(depth, 4)];

@@ -120,7 +120,7 @@ def test_box2d_fast_kernel(r, kon, koff, T, dtype):
     check_case((170, 2312), r, "box", _coeffs(2, r, "box"), T, dtype, 3, kon, koff, 0)
 
 
-@pytest.mark.parametrize("r,kon", [(1, 8), (2, 4), (3, 3), (4, 2)])
+@pytest.mark.parametrize("r,kon", [(1, 8), (2, 4), (3, 3), (4, 2), (1, 4), (2, 2), (3, 1), (4, 1)])
 def test_box2d_fast_kernel_matches_generic_kernel_bitwise(r, kon, monkeypatch):
     """Both kernels sum each cell's products in the same order (row by row
     from offset (-R, -R), a multiply first), so their FP32 results agree bit
