@@ -11,8 +11,18 @@ transfers, the on-chip temporal-blocking kernels over the circular
 region-sharing buffer, device-to-host transfers.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl so2dr|reference]
-                  [--config c2|c1|c3|c4-bf16|c4-f16|c4-f32] [--k-off k] [--k-on k]
-  python bench.py --kernel-case 512 --k-on 4      # in-core kernel run (profiling)
+                  [--config c2|c1|c3|c4-bf16|c4-f16|c4-f32|c5|box2d{1..4}r|box2d{1..4}r-ic]
+                  [--mode so2dr|incore|resreu] [--k-off k] [--k-on k]
+                  [--tune N] [--timeline FILE] [--no-cpu-baseline]
+  python bench.py --sweep 4,8,16,32 [--k-on 4]    # run-time tuning trade-off (Sec. V-B)
+  python bench.py --link                          # host link: copy engines vs SM copies
+  python bench.py --kernel-case 512 --k-on 4 [--kind box --radius R]
+                                                  # in-core kernel run (profiling)
+
+--mode resreu runs the redundancy-free comparison code (single-step launches,
+region sharing of intermediate results); --mode incore the in-core code (whole
+grid on the device, transfers outside the timed region).  --tune N times the
+cost model's N best plans (so2dr_autotune) and benchmarks the fastest.
 
 k_off / k_on of 0 let the planner choose them (and its buffer options) from its
 cost model calibrated to the measured kernel rates.

@@ -85,3 +85,13 @@ def test_measure_link_rejects_bad_arguments_before_any_device_work():
     assert lib.so2dr_measure_link(buf, buf, buf, (1 << 20) + 8, 64, 1, out) == so2dr.E_INVAL  # not 16-byte multiple
     assert lib.so2dr_measure_link(buf, buf, buf, 1 << 20, 0, 1, out) == so2dr.E_INVAL
 
+
+def test_timeline_is_empty_before_any_timed_run():
+    import ctypes
+    lib = so2dr.load_library()
+    p = so2dr.Plan((40, 36, 44), 1, "star", C7, 4, min_chunks=3, budget_bytes=0)
+    n = ctypes.c_int64(-1)
+    assert lib.so2dr_run_timeline(p._h, None, None, 0, ctypes.byref(n)) == so2dr.OK
+    assert n.value == 0
+    assert lib.so2dr_run_timeline(None, None, None, 0, ctypes.byref(n)) == so2dr.E_INVAL
+
