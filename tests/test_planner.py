@@ -137,3 +137,25 @@ def test_varcoef_plan_rejects_budgets_the_adjoint_cannot_fit():
         so2dr.Plan((16, 12, 16), 1, "varcoef", None, 5, min_chunks=1, k_on=2, k_off=1, budget_bytes=40 << 10,
                    dtype="f32")
     assert e.value.code == so2dr.E_INFEASIBLE and "adjoint" in str(e.value)
+
+
+def test_beyond_hbm_grid_plans_within_the_budget():
+    """The optional beyond-HBM run of the radius-4 workload, 4096 x 4096 x 3200
+    FP32 (214.7 GB, more than one GB300's HBM), plans under a 4 GiB budget:
+    every plane crosses the link once per round, and the arena fits."""
+    dims, T, budget = (3200, 4096, 4096), 32, 4 << 30
+    c = np.full(25, 1.0 / 25)
+    p = so2dr.Plan(dims, 4, "star", c, T, min_chunks=1, budget_bytes=budget, dtype="f32",
+                   link_gbs=(171.35, 171.35), hbm_gbs=6781.4)
+    info = p.info
+    assert info["arena_bytes"] <= budget and info["chunks"] >= 2
+    assert info["plane_bytes"] == 4096 * 4096 * 4
+    ops = p.ops()
+    n0 = dims[0]
+    for t in range(info["rounds"]):
+        h2d = np.zeros(n0, int)
+        for o in ops:
+            if o["round"] == t and o["kind"] == 0:
+                h2d[o["src_lo"]:o["src_hi"]] += 1
+        assert np.all(h2d == 1)
+    assert info["h2d_bytes_per_run"] == info["rounds"] * n0 * info["plane_bytes"]
