@@ -159,3 +159,37 @@ def test_beyond_hbm_grid_plans_within_the_budget():
                 h2d[o["src_lo"]:o["src_hi"]] += 1
         assert np.all(h2d == 1)
     assert info["h2d_bytes_per_run"] == info["rounds"] * n0 * info["plane_bytes"]
+
+
+@pytest.mark.parametrize("dims,r,kind,T,dmin,kon,koff,budget", [
+    ((48, 40), 1, "star", 16, 4, 4, 8, 0),
+    ((70, 12, 14), 1, "star", 11, 7, 4, 8, 0),
+    ((64, 14, 15), 4, "star", 5, 3, 2, 5, 0),
+    ((90, 40), 2, "box", 9, 3, 3, 4, 0),
+    ((512, 512), 1, "star", 16, 4, 4, 8, 1 << 20),
+    ((256, 128, 128), 1, "star", 32, 1, 0, 0, 16 << 20),
+    ((40, 16), 1, "star", 10, 38, 4, 10, 0),
+])
+def test_arena_buffers_are_aligned_disjoint_and_inside_the_arena(dims, r, kind, T, dmin, kon, koff, budget):
+    """Every buffer of every run mode lies inside that mode's arena, starts on
+    a 256-byte boundary and overlaps no other buffer (guard against layout
+    bugs that would let one stage overwrite another's planes)."""
+    n = 1 + 2 * r * len(dims) if kind == "star" else (2 * r + 1) ** 2
+    p = so2dr.Plan(dims, r, kind, np.full(n, 1.0 / n), T, min_chunks=dmin, k_on=kon, k_off=koff,
+                   budget_bytes=budget, dtype="f32")
+    info = p.info
+    arenas = {0: info["arena_bytes"], 1: info["arena_bytes_in_core"], 2: info["arena_bytes_result_reuse"]}
+    for mode, arena in arenas.items():
+        if mode == 2 and not info["result_reuse_chunks"]:
+            continue
+        spans = []
+        for off, cap in p.buffers(mode):
+            assert off % 256 == 0 and cap >= 0
+            if cap:
+                spans.append((off, off + cap * info["plane_bytes"]))
+        spans.sort()
+        assert spans and spans[-1][1] <= arena, (mode, spans[-1], arena)
+        for (a0, a1), (b0, b1) in zip(spans, spans[1:]):
+            assert a1 <= b0, (mode, (a0, a1), (b0, b1))
+        if budget and mode == 0:
+            assert arena <= budget
