@@ -17,7 +17,7 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 LIB = os.path.join(HERE, "libso2dr.so")
 BUILD_DIR = os.path.join(HERE, "_build")
 
-CU_SOURCES = ["run.cu", "kernels.cu", "adjoint.cu", "noalloc.cu", "tune.cu", "stencil_f64.cu", "stencil_f32.cu",
+CU_SOURCES = ["run.cu", "kernels.cu", "tma_map.cu", "adjoint.cu", "noalloc.cu", "tune.cu", "stencil_f64.cu", "stencil_f32.cu",
               "stencil_bf16.cu", "stencil_f16.cu"]
 CXX_SOURCES = ["plan.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

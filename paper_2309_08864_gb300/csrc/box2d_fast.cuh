@@ -29,7 +29,8 @@
 //    generic kernel -- so every launch, tile and chunk rounds identically.
 #pragma once
 
-#include "star3d_fast.cuh"
+#include "stencil.cuh"
+#include "tb_common.cuh"
 
 namespace so2dr {
 
@@ -182,10 +183,13 @@ struct FastBox {
     __device__ __forceinline__ void level(int p, const T* sbuf, int buf) {
         const int zp = za + p - L * (R + 1);
         const int lo = need_lo - (K - L) * R, hi = need_hi + (K - L) * R;
-        if (zp < za || zp < lo || zp >= hi) {
-            if constexpr (L + 1 < K) level<L + 1, PH>(p, sbuf, buf);
-            return;
-        }
+        if (!(zp < za || zp < lo || zp >= hi)) level_body<L, PH>(p, sbuf, buf);
+        if constexpr (L + 1 < K) level<L + 1, PH>(p, sbuf, buf);
+    }
+
+    template <int L, int PH>
+    __device__ __forceinline__ void level_body(int p, const T* sbuf, int buf) {
+        const int zp = za + p - L * (R + 1);
         float f[NF];
         float2 done[2];
         const int zt = zp - R;
@@ -204,7 +208,6 @@ struct FastBox {
             *reinterpret_cast<float4*>(slev + (L * NB + buf) * ROW + PAD + 4 * tid) =
                 make_float4(done[0].x, done[0].y, done[1].x, done[1].y);
         }
-        if constexpr (L + 1 < K) level<L + 1, PH>(p, sbuf, buf);
     }
 
     template <int PH>

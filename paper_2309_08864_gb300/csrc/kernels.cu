@@ -1,7 +1,7 @@
 // kernels.cu -- launch geometry and dtype dispatch of the stencil kernel.
 #include "kernels.hpp"
 #include "box2d_fast.cuh"
-#include "star3d_fast.cuh"
+#include "star3d_tb.cuh"
 
 #include <cstdlib>
 
@@ -25,6 +25,8 @@ bool fast_star3d_supported(int r, int depth) {
            ((r == 3 || r == 4) && depth == 1);
 }
 
+bool fast_star3d_row_ok(int64_t nx, int esize) { return nx % (esize == 4 ? 4 : 8) == 0; }
+
 bool fast_box2d_supported(int r, int depth) {
     return depth >= 1 && ((r == 1 && depth <= 8) || (r == 2 && depth <= 4) || (r == 3 && depth <= 3) ||
                           (r == 4 && depth <= 2));
@@ -45,12 +47,12 @@ template <int R, int K> void box_shape(LaunchShape& ls, int64_t nx, int esize) {
 }
 
 template <int R, int K> void fast_shape(LaunchShape& ls, int64_t ny, int64_t nx, int esize) {
-    using S = FastShape<R, K>;
+    using S = StarShape<R, K>;
     ls.lx = S::LX;
     ls.ly = S::LYT;
     ls.tx = S::TX;
     ls.ty = S::TY;
-    ls.block = dim3(S::NW * 32, 1, 1);
+    ls.block = dim3(S::NT, 1, 1);
     ls.smem = esize == 4 ? S::template smem<4>() : S::template smem<2>();
     ls.grid = dim3((unsigned)((nx + S::TX - 1) / S::TX), (unsigned)((ny + S::TY - 1) / S::TY), 1);
     ls.ok = ls.grid.y <= 65535;
@@ -86,7 +88,7 @@ LaunchShape stencil_launch_shape(int shape, int r, int depth, int64_t ny, int64_
         }
         if (ls.ok) return ls;
     }
-    if (shape == kStar3D && csize == 4 && nx % 4 == 0 && fast_star3d_supported(r, depth) &&
+    if (shape == kStar3D && csize == 4 && fast_star3d_row_ok(nx, esize) && fast_star3d_supported(r, depth) &&
         !std::getenv("SO2DR_GENERIC_KERNEL")) {
         switch (r * 16 + depth) {
             case 17: fast_shape<1, 1>(ls, ny, nx, esize); break;

@@ -1,6 +1,7 @@
 // kernels.hpp -- host-side entry points of the device kernels.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include "so2dr.h"
@@ -14,13 +15,23 @@ struct LaunchShape {
     size_t smem;
     int lx, ly, tx, ty;
     bool ok;
-    int fast;    // 0 generic kernel, kFastStar3D (star3d_fast.cuh), kFastBox2D (box2d_fast.cuh)
+    int fast;    // 0 generic kernel, kFastStar3D (star3d_tb.cuh), kFastBox2D (box2d_fast.cuh)
 };
 
 constexpr int kFastStar3D = 1, kFastBox2D = 2;
 
 // (R, K) pairs the register-streaming 3D star kernel is instantiated for.
 bool fast_star3d_supported(int r, int depth);
+
+// Whether the 3D star kernel can stage planes of this row length with TMA:
+// rows must be a whole number of 16-byte units (nx % 4 == 0 for 4-byte
+// storage, nx % 8 == 0 for 16-bit storage).
+bool fast_star3d_row_ok(int64_t nx, int esize);
+
+// TMA descriptor of a buffer of `cap` planes of ny x nx elements of `esize`
+// bytes, with boxes of box_x columns x box_rows rows x 1 plane.  Host only.
+cudaError_t encode_plane_map(CUtensorMap* map, int esize, const void* base, int64_t nx, int64_t ny, int64_t cap,
+                             int box_x, int box_rows);
 
 // (R, K) pairs the register-streaming 2D box kernel is instantiated for.
 bool fast_box2d_supported(int r, int depth);

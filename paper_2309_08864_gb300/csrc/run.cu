@@ -205,7 +205,7 @@ int enqueue_stencil(so2dr_plan_s* P, const RunList& rl, const Op& op, cudaStream
     a.ly = ls.ly;
     a.tx = ls.tx;
     a.ty = ls.ty;
-    a.status = nullptr;
+    a.status = reinterpret_cast<int*>(P->arena + rl.arena_bytes - kAlign);  // the run list's status word
     for (size_t k = 0; k < p.coeffs.size() && k < (size_t)kMaxCoeffsDev; ++k) {
         a.c[k] = p.coeffs[k];
         a.cf[k] = (float)p.coeffs[k];
@@ -238,6 +238,11 @@ int execute(so2dr_plan_s* P, const RunList& rl, char* const* hosts, const int64_
         if (rc) return rc;
     }
     cudaStream_t* st = P->st;
+    // device status word (the last kAlign bytes of the run list's arena): a
+    // kernel whose bounded wait for a copy gave up sets it
+    int* status = reinterpret_cast<int*>(P->arena + rl.arena_bytes - kAlign);
+    if ((e = cudaMemsetAsync(status, 0, sizeof(int), st[kStreamH2D])) != cudaSuccess)
+        return cuda_fail(e, "cudaMemsetAsync(status)");
     // start marker: the compute and D2H streams start after everything the
     // caller queued on the H2D stream
     cudaEvent_t start = P->join[0];
@@ -305,6 +310,10 @@ int execute(so2dr_plan_s* P, const RunList& rl, char* const* hosts, const int64_
     }
     int rc = bounded_wait(ends, wait_timeout_s());
     if (rc) return rc;
+    int hstatus = 0;
+    if ((e = cudaMemcpy(&hstatus, status, sizeof(int), cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return cuda_fail(e, "status read");
+    if (hstatus) return set_error(SO2DR_E_TIMEOUT, "a kernel's wait for a staged plane gave up");
     if (timing) {
         float ms = 0;
         std::memset(stats, 0, sizeof(*stats));

@@ -1,0 +1,397 @@
+// star3d_tb.cuh -- register-streaming temporal-blocking kernel for 3D star
+// stencils (radius R, K fused steps per launch), FP32 arithmetic on FP32 /
+// BF16 / FP16 storage.
+//
+// The on-chip temporal blocking of Sec. III / Sec. IV-A, laid out for sm_103a:
+//  * a CTA owns a 128-wide x tile (32 lanes x 4 cells) and NW*VY rows of y
+//    (VY rows per warp) and streams the planes of axis 0 through it; a launch
+//    may split axis 0 into segments (gridDim.z) so that the grid fills the
+//    SMs evenly;
+//  * each input plane is read from device memory once, as one TMA box
+//    (cp.async.bulk.tensor, issued by one thread, landing on an mbarrier) of
+//    the tile plus R halo rows, PD planes ahead of its use in an NI-slot ring;
+//    the box reads zeros where it leaves the grid;
+//  * every fused level keeps 2R partial sums per cell in registers: when the
+//    level below produces plane z', it is added into the targets z'-R..z'+R
+//    (the in-plane terms at z') and target z'-R is complete.  The register
+//    slot of a target is fixed by its plane index modulo 2R and the plane
+//    loop is unrolled 2R times, so the ring never moves data;
+//  * levels are pipelined across planes: level L consumes what level L-1
+//    completed in the previous phase (two shared-memory plane slots per
+//    level), so one barrier per plane suffices; y neighbours come from
+//    shared memory, x neighbours from warp shuffles;
+//  * every cell is computed as if interior.  Cells of the fixed boundary
+//    (the in-plane ring of width R and the first and last R planes) keep
+//    their value: in warps or planes that hold such cells, the centre
+//    arrival of a boundary target stores the arriving value and the later
+//    arrivals leave it alone (per-cell selects on a slower path that only
+//    boundary warps and edge planes take);
+//  * phases in which every level is active and no boundary plane is in
+//    flight run a straight-line body without per-level tests.
+// The valid area shrinks by R per level in y and x: the compute-area
+// adjustment of Algorithm 1 applied inside a launch.
+//
+// Per-cell arithmetic order (identical in every launch, chunk and tile, and
+// the order of the generic kernel in stencil.cuh):
+//   c(-R e0) u, then FMAs with c(-R+1 e0) ... c(-e0), c(0), c(-e1), c(+e1),
+//   ..., c(-R e1), c(+R e1), c(-e2), c(+e2), ..., c(+e0), ..., c(+R e0).
+#pragma once
+
+#include "stencil.cuh"
+#include "tb_common.cuh"
+
+namespace so2dr {
+
+// Tile shape per (R, K): 16 warps of 2 rows for fused depths (8 warps for one
+// level, where no y halo is lost and several CTAs share an SM).  Four fused
+// levels of radius 1 keep 64 partial sums per thread, which fits a 512-thread
+// CTA in the register file.
+template <int R, int K> struct StarShape {
+    static constexpr int VY = 2;
+    static constexpr int NW = K == 1 ? 8 : 16;
+    static constexpr int NT = NW * 32;
+    static constexpr int LX = 128;                      // tile columns (32 lanes x 4)
+    static constexpr int LYT = NW * VY;                 // tile rows
+    static constexpr int HXA = ((R * K + 3) / 4) * 4;   // x halo, whole 4-cell vectors
+    static constexpr int HY = R * (K - 1);              // rows lost per side to the y halo
+    static constexpr int TX = LX - 2 * HXA;             // output columns per tile
+    static constexpr int TY = LYT - 2 * HY;             // output rows per tile
+    static constexpr int ROWS = LYT + 2 * R;            // staged input rows / level-plane rows
+    static constexpr int NI = 4;                        // input plane slots
+    static constexpr int PD = NI - 1;                   // planes loaded ahead
+    static constexpr int NB = 2;                        // plane slots per intermediate level
+    static constexpr int MINB = K == 1 ? 2 : 1;         // CTAs per SM the registers are sized for
+    // staged columns: 16-bit boxes start on an 8-element boundary (16 bytes),
+    // so they carry 8 spare columns and the tile starts 0 or 4 columns in
+    template <int ES> static constexpr int lxb() { return ES == 4 ? LX : LX + 8; }
+    template <int ES> static constexpr int box_bytes() { return lxb<ES>() * ROWS * ES; }
+    template <int ES> static constexpr int in_slot_bytes() { return (box_bytes<ES>() + 127) / 128 * 128; }
+    static constexpr int lev_bytes = ROWS * LX * 4;
+    static constexpr int kBarBytes = 128;               // NI mbarriers, padded
+    template <int ES> static constexpr int smem() {
+        return kBarBytes + NI * in_slot_bytes<ES>() + (K - 1) * NB * lev_bytes;
+    }
+};
+
+template <typename T, int R, int K>
+struct StarTB {
+    using S = StarShape<R, K>;
+    static constexpr int VY = S::VY, NW = S::NW, LX = S::LX, LYT = S::LYT, ROWS = S::ROWS, NI = S::NI,
+                         PD = S::PD, NB = S::NB, W2 = 2 * R, ES = (int)sizeof(T), LXB = S::template lxb<ES>(),
+                         SLOT = S::template in_slot_bytes<ES>();
+    static constexpr unsigned kAll = (1u << (4 * VY)) - 1u;
+
+    const StencilArgs& a;
+    const CUtensorMap* tmap;
+    uint32_t bar0, sin0;  // shared addresses: mbarrier 0, input slot 0
+    const T* sin;         // [NI] slots of [ROWS][LXB] staged input
+    float* slev;          // [K-1][NB][ROWS][LX] completed planes of levels 0..K-2
+    int lane, warp, my_row, col0;
+    int n0, ny, nx, xs, ys, gx0, bx0;
+    int za, zb, olo, ohi, need_lo, need_hi;
+    int ps_lo, ps_hi;     // phases in which every level is active
+    int pfail;            // phase whose input copy did not land in time
+    int64_t plane;
+    bool xin, warp_bnd;
+    unsigned inyx;        // bit y*4+e: my cell (row y, column e) is interior in its plane
+    T* out;
+    float2 A[K][W2][VY][2];  // 2R partial sums per cell per level, in x pairs
+
+    __device__ __forceinline__ explicit StarTB(const StencilArgs& args, const CUtensorMap* m) : a(args), tmap(m) {}
+
+    // first and one-past-last arrival plane level L needs
+    __device__ __forceinline__ int lev_lo(int L) const {
+        const int v = need_lo - (K - L) * R;
+        return v > za ? v : za;
+    }
+    __device__ __forceinline__ int lev_hi(int L) const { return need_hi + (K - L) * R; }
+
+    // boundary mask (bits y*4+e) of target plane zt: every cell of a fixed
+    // plane, else the in-plane ring
+    __device__ __forceinline__ unsigned bmask(int zt) const {
+        return (zt < R || zt >= n0 - R) ? kAll : (~inyx & kAll);
+    }
+
+    // one thread: TMA of the input plane of phase q into its slot
+    __device__ __forceinline__ void issue(int q) {
+        const int z = za + q;
+        if (z >= zb) return;
+        const int slot = (int)((a.in_slot0 + (int64_t)(z - (int)a.in_lo)) % a.in_cap);
+        const uint32_t bar = bar0 + (uint32_t)(q % NI) * 8u;
+        mbar_arrive_expect_tx(bar, (uint32_t)S::template box_bytes<ES>());
+        tma_load_3d(sin0 + (uint32_t)(q % NI) * SLOT, tmap, bx0, ys - R, slot, bar);
+    }
+
+    __device__ __forceinline__ static float2 sel2(unsigned m, int bit, float2 keep, float2 nv) {
+        return make_float2(((m >> bit) & 1u) ? keep.x : nv.x, ((m >> (bit + 1)) & 1u) ? keep.y : nv.y);
+    }
+
+    // One arrival at level L whose target phase is PHL = (zp - za) mod 2R:
+    // v holds my cells of the arriving plane, `rows` its shared-memory copy
+    // (tile row t at row t + R, my first column at element col).  Boundary
+    // masks mz[t] (t = 0..R) belong to targets zp - R + t (BND only).
+    template <int L, int PHL, bool BND, typename ST>
+    __device__ __forceinline__ void arrive(const float2 (&v)[VY][2], const ST* rows, int pitch, int col,
+                                           float2 (&done)[VY][2], const unsigned (&mz)[R + 1]) {
+        // x neighbours beyond my 4 cells, from the adjacent lanes
+        float lft[VY][4], rgt[VY][4];
+#pragma unroll
+        for (int y = 0; y < VY; ++y)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const float me = (e & 1) ? v[y][e >> 1].y : v[y][e >> 1].x;
+                lft[y][e] = (e >= 4 - R) ? __shfl_up_sync(0xffffffffu, me, 1) : 0.f;
+                rgt[y][e] = (e < R) ? __shfl_down_sync(0xffffffffu, me, 1) : 0.f;
+            }
+        // y neighbours outside my VY rows, from shared memory
+        float4 up[VY][R], dn[VY][R];
+#pragma unroll
+        for (int y = 0; y < VY; ++y)
+#pragma unroll
+            for (int j = 1; j <= R; ++j) {
+                if (y - j < 0) up[y][j - 1] = lds4(rows + (my_row + y - j + R) * pitch + col);
+                if (y + j >= VY) dn[y][j - 1] = lds4(rows + (my_row + y + j + R) * pitch + col);
+            }
+        auto xval = [&](int y, int e) -> float {
+            if (e < 0) return lft[y][4 + e];
+            if (e > 3) return rgt[y][e - 4];
+            return (e & 1) ? v[y][e >> 1].y : v[y][e >> 1].x;
+        };
+        auto xpair = [&](int y, int e) -> float2 {
+            if (e == 0 || e == 2) return v[y][e >> 1];
+            return make_float2(xval(y, e), xval(y, e + 1));
+        };
+        auto ypair = [&](int y, int j, int h) -> float2 {
+            if (y + j >= 0 && y + j < VY) return v[y + j][h];
+            const float4 q = (j < 0) ? up[y][-j - 1] : dn[y][j - 1];
+            return h ? make_float2(q.z, q.w) : make_float2(q.x, q.y);
+        };
+        // target t is plane zp - R + t, kept in slot (PHL - R + t) mod 2R;
+        // cells go in x pairs through packed FP32x2 FMAs (each lane an
+        // ordinary fused multiply-add, so the per-cell order is unchanged)
+#pragma unroll
+        for (int y = 0; y < VY; ++y)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int e0 = 2 * h, bit = 4 * y + 2 * h;
+                const float2 x = v[y][h];
+#pragma unroll
+                for (int t = R + 1; t < 2 * R; ++t) {
+                    float2& acc = A[L][pmod(PHL - R + t, W2)][y][h];
+                    acc = __ffma2_rn(a.cf2[cidx<R>(0, -1, t - R)], x, acc);
+                }
+                {
+                    float2& acc = A[L][pmod(PHL, W2)][y][h];
+                    float2 s2 = __ffma2_rn(a.cf2[0], x, acc);
+#pragma unroll
+                    for (int j = 1; j <= R; ++j) {
+                        s2 = __ffma2_rn(a.cf2[cidx<R>(1, -1, j)], ypair(y, -j, h), s2);
+                        s2 = __ffma2_rn(a.cf2[cidx<R>(1, +1, j)], ypair(y, +j, h), s2);
+                    }
+#pragma unroll
+                    for (int j = 1; j <= R; ++j) {
+                        s2 = __ffma2_rn(a.cf2[cidx<R>(2, -1, j)], xpair(y, e0 - j), s2);
+                        s2 = __ffma2_rn(a.cf2[cidx<R>(2, +1, j)], xpair(y, e0 + j), s2);
+                    }
+                    // a boundary target keeps the value of its centre arrival
+                    acc = BND ? sel2(mz[R], bit, x, s2) : s2;
+                }
+#pragma unroll
+                for (int t = 1; t < R; ++t) {
+                    float2& acc = A[L][pmod(PHL - R + t, W2)][y][h];
+                    const float2 nv = __ffma2_rn(a.cf2[cidx<R>(0, +1, R - t)], x, acc);
+                    acc = BND ? sel2(mz[t], bit, acc, nv) : nv;
+                }
+                float2& a0 = A[L][pmod(PHL - R, W2)][y][h];
+                const float2 fin = __ffma2_rn(a.cf2[cidx<R>(0, +1, R)], x, a0);
+                done[y][h] = BND ? sel2(mz[0], bit, a0, fin) : fin;
+                a0 = __fmul2_rn(a.cf2[cidx<R>(0, -1, R)], x);  // first contribution to target zp + R
+            }
+    }
+
+    __device__ __forceinline__ void emit(const float2 (&done)[VY][2], int zt) {
+        if (zt < olo || zt >= ohi) return;
+        const int lx0 = lane * 4;
+        if (!(lx0 >= S::HXA && lx0 < S::HXA + S::TX && xin)) return;
+        T* ob = out + (int64_t)(zt - (int)a.out_lo) * plane;
+#pragma unroll
+        for (int y = 0; y < VY; ++y) {
+            const int ty = my_row + y, gy = ys + ty;
+            if (ty >= S::HY && ty < S::HY + S::TY && gy < ny)
+                st4(ob + (int64_t)gy * nx + gx0, make_float4(done[y][0].x, done[y][0].y, done[y][1].x, done[y][1].y));
+        }
+    }
+
+    // level L of phase p (PH = p mod 2R; p0 is a multiple of 2R, so the
+    // parity of p is that of PH): consumes input plane za + p (L = 0) or what
+    // level L-1 completed in phase p-1 (plane za + p - L(R+1))
+    template <int L, int PH, bool BND>
+    __device__ __forceinline__ void level_body(int p) {
+        const int zp = za + p - L * (R + 1);
+        unsigned mz[R + 1];
+#pragma unroll
+        for (int t = 0; t <= R; ++t) mz[t] = BND ? bmask(zp - R + t) : 0u;
+        float2 v[VY][2], done[VY][2];
+        constexpr int PHL = pmod(PH - L * (R + 1), W2);
+        if constexpr (L == 0) {
+            const T* rows = sin + (p % NI) * (SLOT / ES);
+#pragma unroll
+            for (int y = 0; y < VY; ++y) {
+                const float4 q = lds4(rows + (my_row + y + R) * LXB + col0);
+                v[y][0] = make_float2(q.x, q.y);
+                v[y][1] = make_float2(q.z, q.w);
+            }
+            arrive<0, PHL, BND>(v, rows, LXB, col0, done, mz);
+        } else {
+            const float* prev = slev + ((L - 1) * NB + ((PH + 1) & 1)) * ROWS * LX;  // slot of phase p-1
+#pragma unroll
+            for (int y = 0; y < VY; ++y) {
+                const float4 q = lds4(prev + (my_row + y + R) * LX + lane * 4);
+                v[y][0] = make_float2(q.x, q.y);
+                v[y][1] = make_float2(q.z, q.w);
+            }
+            arrive<L, PHL, BND>(v, prev, LX, lane * 4, done, mz);
+        }
+        if constexpr (L == K - 1) {
+            emit(done, zp - R);
+        } else {
+            float* lb = slev + (L * NB + (PH & 1)) * ROWS * LX;
+#pragma unroll
+            for (int y = 0; y < VY; ++y)
+                *reinterpret_cast<float4*>(lb + (my_row + y + R) * LX + lane * 4) =
+                    make_float4(done[y][0].x, done[y][0].y, done[y][1].x, done[y][1].y);
+        }
+    }
+
+    // every level active, no boundary cell or plane in flight
+    template <int L, int PH>
+    __device__ __forceinline__ void levels_fast(int p) {
+        level_body<L, PH, false>(p);
+        if constexpr (L + 1 < K) levels_fast<L + 1, PH>(p);
+    }
+
+    // head and tail of the stream, edge planes and boundary warps
+    template <int L, int PH>
+    __device__ __forceinline__ void levels_checked(int p) {
+        const int zp = za + p - L * (R + 1);
+        if (zp >= lev_lo(L) && zp < lev_hi(L)) {
+            if (warp_bnd || zp < 2 * R || zp >= n0 - R) level_body<L, PH, true>(p);
+            else level_body<L, PH, false>(p);
+        }
+        if constexpr (L + 1 < K) levels_checked<L + 1, PH>(p);
+    }
+
+    // phase p = p0 + PH; false when an input copy did not land in time
+    template <int PH>
+    __device__ __forceinline__ bool phase(int p0) {
+        const int p = p0 + PH;
+        bool late = false;
+        if (za + p < zb) late = !mbar_wait_bounded(bar0 + (uint32_t)(p % NI) * 8u, (uint32_t)((p / NI) & 1));
+        if (__syncthreads_or(late)) {
+            pfail = p;
+            return false;
+        }
+        // the slot of phase p + PD last held phase p - 1, read before the barrier
+        if (threadIdx.x == 0) {
+            fence_proxy_async_smem();
+            issue(p + PD);
+        }
+        const int zmin = za + p - (K - 1) * (R + 1), zmax = za + p;
+        if (p >= ps_lo && p < ps_hi && !warp_bnd && zmin >= 2 * R && zmax < n0 - R) levels_fast<0, PH>(p);
+        else levels_checked<0, PH>(p);
+        if constexpr (PH + 1 < W2) return phase<PH + 1>(p0);
+        return true;
+    }
+
+    __device__ __forceinline__ void run(unsigned char* smem) {
+        bar0 = smem_u32(smem);
+        sin = reinterpret_cast<const T*>(smem + S::kBarBytes);
+        sin0 = bar0 + S::kBarBytes;
+        slev = reinterpret_cast<float*>(smem + S::kBarBytes + NI * SLOT);
+        lane = threadIdx.x & 31;
+        warp = threadIdx.x >> 5;
+        my_row = warp * VY;
+        const int x0 = (int)blockIdx.x * S::TX, y0 = (int)blockIdx.y * S::TY;
+        xs = x0 - S::HXA;
+        ys = y0 - S::HY;
+        ny = (int)a.ny;
+        nx = (int)a.nx;
+        plane = a.ny * a.nx;
+        n0 = (int)a.n0;
+        gx0 = xs + lane * 4;
+        xin = gx0 >= 0 && gx0 < nx;  // nx % 4 == 0: a vector is all in or all out
+        bx0 = ES == 4 ? xs : (xs & ~7);  // 16-byte aligned box start
+        col0 = (xs - bx0) + lane * 4;
+        out = static_cast<T*>(a.out);
+        inyx = 0;
+#pragma unroll
+        for (int y = 0; y < VY; ++y)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int gy = ys + my_row + y, gx = gx0 + e;
+                if (gy >= R && gy < ny - R && gx >= R && gx < nx - R) inyx |= 1u << (y * 4 + e);
+            }
+        warp_bnd = __any_sync(0xffffffffu, inyx != kAll);
+#pragma unroll
+        for (int l = 0; l < K; ++l)
+#pragma unroll
+            for (int q = 0; q < W2; ++q)
+#pragma unroll
+                for (int y = 0; y < VY; ++y)
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) A[l][q][y][h] = make_float2(0.f, 0.f);
+        // axis-0 segment of this CTA: outputs [zs, ze), stream over [za, zb)
+        const int nseg = gridDim.z;
+        const int nout = (int)(a.out_hi - a.out_lo), in_lo = (int)a.in_lo, in_hi = (int)a.in_hi;
+        const int zs = (int)a.out_lo + (int)((int64_t)nout * blockIdx.z / nseg);
+        const int ze = (int)a.out_lo + (int)((int64_t)nout * (blockIdx.z + 1) / nseg);
+        za = zs - K * R > in_lo ? zs - K * R : in_lo;
+        zb = ze + K * R < in_hi ? ze + K * R : in_hi;
+        olo = need_lo = zs;
+        ohi = need_hi = ze;
+        // phases in which every level is active: level L handles arrival
+        // za + p - L(R+1) in phase p
+        ps_lo = 0;
+        ps_hi = 1 << 30;
+#pragma unroll
+        for (int L = 0; L < K; ++L) {
+            const int lo = lev_lo(L) - za + L * (R + 1), hi = lev_hi(L) - za + L * (R + 1);
+            ps_lo = lo > ps_lo ? lo : ps_lo;
+            ps_hi = hi < ps_hi ? hi : ps_hi;
+        }
+        // last arrival any level needs: level K-1 at plane need_hi + R - 1
+        const int nph0 = (need_hi + R - 1 - za) + (K - 1) * (R + 1) + 1;
+        const int nph = (nph0 + W2 - 1) / W2 * W2;
+        if (threadIdx.x == 0) {
+#pragma unroll
+            for (int i = 0; i < NI; ++i) mbar_init(bar0 + 8u * i, 1);
+            fence_mbar_init();
+        }
+        __syncthreads();
+        if (threadIdx.x == 0)
+            for (int q = 0; q < PD; ++q) issue(q);
+        bool ok = true;
+        for (int p0 = 0; p0 < nph && ok; p0 += W2) ok = phase<0>(p0);
+        if (!ok) {
+            // a copy did not land: report it and wait (bounded) for the
+            // copies still in flight before the shared memory is released
+            if (threadIdx.x == 0) {
+                if (a.status) atomicOr(a.status, 1);
+                // phases pfail .. pfail + PD - 1 were issued and not consumed
+                for (int q = pfail; q < pfail + PD && za + q < zb; ++q)
+                    (void)mbar_wait_bounded(bar0 + (uint32_t)(q % NI) * 8u, (uint32_t)((q / NI) & 1));
+            }
+            __syncthreads();
+        }
+    }
+};
+
+template <typename T, int R, int K>
+__global__ void __launch_bounds__(StarShape<R, K>::NT, StarShape<R, K>::MINB)
+    star3d_tb_kernel(const StencilArgs a, const __grid_constant__ CUtensorMap tmap) {
+    extern __shared__ __align__(1024) unsigned char smem_tb[];
+    StarTB<T, R, K> k(a, &tmap);
+    k.run(smem_tb);
+}
+
+}  // namespace so2dr
