@@ -398,22 +398,27 @@ int so2dr_dot(so2dr_plan_t plan, const void* host_a, const void* host_b, int64_t
  * Runs `steps` time steps of a constant-coefficient star stencil (2D or 3D)
  * or 2D box stencil, of the given radius, coefficient table (see so2dr_kind)
  * and storage dtype, on a grid that is already on the device: d_in is read,
- * d_out receives the result (distinct, caller-owned device buffers of
- * dims[0]*dims[1](*dims[2]) elements; d_in is not modified).  Launch depths
- * follow Algorithm 1: floor(steps/k_on) k_on-step launches, then the
- * residual, on `stream` (a cudaStream_t; NULL = the legacy default stream).
- * The call returns once the launches are queued; it does not synchronise.
+ * d_out receives the result (caller-owned device buffers of
+ * dims[0]*dims[1](*dims[2]) elements, 16-byte aligned and not overlapping;
+ * d_in is not modified).  The launches are floor(steps/k_on) launches of
+ * depth k_on, then one of the remainder, on `stream` (a cudaStream_t; NULL =
+ * the legacy default stream).  The call returns once the launches are queued;
+ * it does not synchronise.
  *
  * It calls no cudaMalloc, cudaFree or other allocating routine, on the device
  * or the host.  Its one scratch grid lives in a file-scope device array of
- * 32 MiB that every GPU loading the library holds until the process exits:
- * grids above 32 MiB are rejected with SO2DR_E_INFEASIBLE.  The first call
- * on each device looks up that array's device address (cudaGetSymbolAddress
- * with the device current), so make that first call before any stream
- * capture.  Every call shares the array and leaves the last call's data in
- * it (nothing in it has to start at zero: each launch overwrites every cell
- * it later reads); calls whose work overlaps on the GPU race on it, so
- * serialise them (one stream, or events).
+ * 32 MiB that every GPU loading the library holds until the process exits.
+ * Only runs of two or more launches use it: those are rejected with
+ * SO2DR_E_INFEASIBLE when the grid is above 32 MiB (a run of one launch, or
+ * of zero steps, takes any size).  The first such call on each device looks
+ * up the array's device address (cudaGetSymbolAddress with the device
+ * current) and caches it with the id of the current context; after a
+ * cudaDeviceReset, or any re-creation of the device's primary context, the
+ * next call looks it up again.  Make those calls before any stream capture.
+ * Every call shares the array and leaves the last call's data in it (nothing
+ * in it has to start at zero: each launch overwrites every cell it later
+ * reads); calls whose work overlaps on the GPU race on it, so serialise them
+ * (one stream, or events).
  */
 int so2dr_run_device_noalloc(int ndim, const int64_t* dims, int radius, int kind, const double* coeffs,
                              int ncoeffs, int64_t steps, int k_on, int dtype, const void* d_in, void* d_out,

@@ -42,16 +42,18 @@ def test_bind_rejects_null_misaligned_arena_and_stream_count():
     (dict(k_on=0), so2dr.E_INVAL),
     (dict(ncoeffs=6), so2dr.E_INVAL),
     (dict(same=True), so2dr.E_INVAL),                 # d_in == d_out
-    (dict(dims=(4096, 64, 64)), so2dr.E_INFEASIBLE),  # 64 MiB > the 32 MiB scratch
+    (dict(out=(1 << 20) + 4096), so2dr.E_INVAL),      # d_out overlaps d_in
+    (dict(out=(2 << 20) + 8), so2dr.E_INVAL),         # d_out not 16-byte aligned
+    (dict(dims=(4096, 64, 64)), so2dr.E_INFEASIBLE),  # 64 MiB > the 32 MiB scratch (two launches)
 ])
 def test_noalloc_argument_checks(change, code):
     a = dict(ndim=3, dims=(16, 16, 16), radius=1, kind=so2dr.STAR, ncoeffs=7, steps=4, k_on=2, dtype=so2dr.F32,
-             same=False)
+             same=False, out=1 << 40)
     a.update(change)
     d = a["dims"]
     rc = lib().so2dr_run_device_noalloc(a["ndim"], _dims(*d), a["radius"], a["kind"], _coeffs(C7), a["ncoeffs"],
                                         a["steps"], a["k_on"], a["dtype"], FAKE,
-                                        FAKE if a["same"] else ctypes.c_void_p(2 << 20), None)
+                                        FAKE if a["same"] else ctypes.c_void_p(a["out"]), None)
     assert rc == code, lib().so2dr_last_error().decode()
 
 
