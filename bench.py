@@ -45,15 +45,18 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 MEASURED = os.path.join(ROOT, "MEASURED_PEAKS.json")
-# DRAM bytes per algorithmic byte of star3d_fast_kernel<float, 1, 4>, from the
-# full ncu capture of a 512^3 in-core launch (dram__bytes_read.sum +
-# dram__bytes_write.sum = 579.49 + 493.90 MB for 1073.74 MB of algorithmic
-# reads and writes); traffic grows with the planes a launch streams, so a
-# launch's traffic is this ratio times its (input + output) plane bytes.
-DRAM_PER_ALG_BYTE_R1K4_F32 = (579.49 + 493.90) / 1073.74
-# host-link bandwidths measured on the GB300 machines with pinned buffers
-# (cudaMemcpyAsync, 4 GiB): host-to-device 211, device-to-host 193, both
-# directions at once 343 GB/s in total.
+KERNEL_SRC = {"star": os.path.join(ROOT, "paper_2309_08864_gb300", "csrc", "star3d_tb.cuh"),
+              "box": os.path.join(ROOT, "paper_2309_08864_gb300", "csrc", "box2d_fast.cuh")}
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per k_on-deep launch
+# of the benchmarked plan, from one ncu capture of the benchmark command (the
+# summaries under profiles/ give the commands), keyed by the first 16 hex
+# digits of the SHA-256 of the kernel source they were taken with: a capture
+# of an older kernel is not reported.
+DRAM_TRAFFIC = {}
+# host-link bandwidths measured earlier on the GB300 machines with pinned
+# buffers (cudaMemcpyAsync, 4 GiB): host-to-device 211, device-to-host 193,
+# both directions at once 343 GB/s in total; reported beside the rates the
+# benchmark measures in its own process
 LINK_H2D_GBS, LINK_D2H_GBS, LINK_BIDIR_GBS = 211.3, 193.4, 342.7
 # FP32 rate of the SM units (no tensor cores: a stencil is not a dense
 # contraction): 152 SMs x 128 FMA lanes x 2 FLOP x 2.07 GHz (maximum SM clock)
@@ -116,6 +119,35 @@ CONFIGS = {
                dims=(512, 512, 512), r=1, coeffs=None, T=64, dtype="f32", budget=256 << 20,
                min_chunks=1, k_on=4, k_off=8, adjoint=True),
 }
+
+
+def source_digest(path):
+    import hashlib
+    try:
+        with open(path, "rb") as f:
+            return hashlib.sha256(f.read()).hexdigest()[:16]
+    except OSError:
+        return None
+
+
+def path_roofline(grid_bytes, rounds, launches, link, hbm_gbs):
+    """Roofline time of a plan: every cell crosses the host link once each way
+    per round (the two directions at the rates measured while both run), and
+    HBM sees the landing write and the read for the transfers plus one read
+    and one write per fused launch."""
+    t_link = max(grid_bytes * rounds / (link["ce_both_h2d"] * 1e9), grid_bytes * rounds / (link["ce_both_d2h"] * 1e9))
+    hbm_bytes = grid_bytes * rounds * (2.0 + 2.0 * launches)
+    t_hbm = hbm_bytes / (hbm_gbs * 1e9)
+    return {"t_roof_s": max(t_link, t_hbm), "t_link_s": t_link, "t_hbm_s": t_hbm, "hbm_bytes": hbm_bytes,
+            "bound": "host-link" if t_link >= t_hbm else "hbm"}
+
+
+def make_plan(cfg, coeffs, so2dr):
+    """The benchmarked plan: k_off / k_on as the config gives them, else the
+    planner's own choice under its default rates (so that the plan does not
+    depend on the box; the parity tests build it through this function)."""
+    return so2dr.Plan(cfg["dims"], cfg["r"], cfg.get("kind", "star"), coeffs, cfg["T"], min_chunks=cfg["min_chunks"],
+                      k_on=cfg["k_on"], k_off=cfg["k_off"], budget_bytes=cfg["budget"], dtype=cfg["dtype"])
 
 
 def coeffs_of(name, inputs):
@@ -217,10 +249,16 @@ def allreduce_max(x, world):
 
 # ------------------------------------------------------------------ CPU oracle
 
-def oracle_sample(cfg, inputs, steps=None, planes=None):
+DTYPE_CODE = {"f64": 0, "f32": 1, "bf16": 2, "f16": 3}
+
+
+def oracle_sample(cfg, inputs, steps=None, planes=None, rounded=True, keep=False):
     """Times the FP64 oracle on a bounded slab of the workload: `planes`
     planes of axis 0 (full extent on the other axes) for `steps` time steps.
-    Returns (cell_updates_per_s, cores, sample description)."""
+    rounded: the slab as the GPU stores it (storage-rounded values, weights
+    rounded to the compute type); else the unrounded draw and exact weights.
+    Returns (cell_updates_per_s, cores, sample description, seconds, output
+    or None)."""
     import numpy as np
     import oracle
     dims = cfg["dims"]
@@ -229,10 +267,16 @@ def oracle_sample(cfg, inputs, steps=None, planes=None):
     n0 = dims[0] if planes is None else min(planes, dims[0])
     sub = (n0,) + tuple(dims[1:])
     u = inputs.draw_box(1, dims, lo=(0,) * nd, hi=sub)
-    c = coeffs_of(cfg["coeffs"], inputs)
+    if cfg.get("zero_ring"):
+        inputs.zero_ring(u, cfg["r"])
+    c = np.asarray(coeffs_of(cfg["coeffs"], inputs), dtype=np.float64)
+    if rounded and cfg["dtype"] != "f64":
+        code = DTYPE_CODE[cfg["dtype"]]
+        u = inputs.storage_to_f64(inputs.to_storage(u, code), code)
+        c = c.astype(np.float32).astype(np.float64)
     kind = 1 if cfg.get("kind") == "box" else 0
     t0 = time.perf_counter()
-    oracle.run(u, c, cfg["r"], kind, T)
+    out = oracle.run(u, c, cfg["r"], kind, T)
     dt = time.perf_counter() - t0
     inner = 1
     for e in sub:
@@ -240,19 +284,71 @@ def oracle_sample(cfg, inputs, steps=None, planes=None):
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     desc = "FP64 oracle on a %s slab of the workload (first %d planes), %d steps" % (
         "x".join(map(str, sub)), n0, T)
-    return inner * T / dt, cores, desc, dt
+    return inner * T / dt, cores, desc, dt, (out if keep else None)
+
+
+def slab_errors(cfg, gpu_out, ref, planes):
+    """Relative L-infinity and L2 error of the GPU result on the part of an
+    oracle slab that the cut does not reach: planes below planes - r(T+1)
+    (a cell depends only on cells within r*T of it; the slab's top r planes
+    act as a fixed ring in the oracle run)."""
+    import numpy as np
+    hi = planes - cfg["r"] * (cfg["T"] + 1)
+    if hi <= cfg["r"]:
+        return None
+    got = gpu_out[:hi]
+    want = ref[:hi]
+    d = got - want
+    return {"rel_linf": float(np.max(np.abs(d)) / np.max(np.abs(want))),
+            "rel_l2": float(np.linalg.norm(d.ravel()) / np.linalg.norm(want.ravel())), "planes": [0, int(hi)]}
 
 
 def oracle_sample_planes(cfg, budget_s, inputs):
     """Slab thickness giving roughly budget_s seconds of oracle work (probe)."""
     dims = cfg["dims"]
     probe_planes = min(dims[0], 2 * cfg["r"] + 8)
-    rate, _, _, _ = oracle_sample(cfg, inputs, steps=2, planes=probe_planes)
+    rate, _, _, _, _ = oracle_sample(cfg, inputs, steps=2, planes=probe_planes)
     plane_cells = 1
     for e in dims[1:]:
         plane_cells *= e
     want = rate * budget_s / (plane_cells * cfg["T"])
     return int(max(2 * cfg["r"] + 2, min(dims[0], want)))
+
+
+def cpu_baseline_leg(cfg, plan, mode, torch, inputs, so2dr):
+    """The FP64 oracle timed on the host cores on a bounded slab of the
+    workload (about 15 s), and the error of this plan's GPU result against
+    it: one more run of the plan, outside the timed region, from the seeded
+    input, compared on the slab's exact part -- with the oracle started from
+    the same storage-rounded input, and from the unrounded draw with exact
+    weights (for FP64 storage the two coincide)."""
+    import numpy as np
+    import oracle
+    oracle.build.build()
+    planes = oracle_sample_planes(cfg, 15.0, inputs)
+    rate, cores, desc, dt, ref = oracle_sample(cfg, inputs, planes=planes, keep=True)
+    if dt < 10.0 and planes < cfg["dims"][0]:
+        # the small probe overstates the per-plane cost: rescale once
+        planes = int(min(cfg["dims"][0], planes * 15.0 / max(dt, 0.05)))
+        rate, cores, desc, dt, ref = oracle_sample(cfg, inputs, planes=planes, keep=True)
+    base = {"value": rate / 1e9, "unit": "Gcell/s", "cores": cores, "kind": "oracle",
+            "sample": desc + " (%.1f s)" % dt}
+    host = make_input(cfg, inputs, so2dr, torch)
+    plan.run(host, in_core=mode)
+    code = DTYPE_CODE[cfg["dtype"]]
+    if cfg["dtype"] == "bf16":
+        gpu = inputs.bf16_bits_to_f64(host[:planes].contiguous().view(torch.int16).numpy().view(np.uint16))
+    else:
+        gpu = host[:planes].numpy().astype(np.float64)
+    err = {"reference": "FP64 oracle from the storage-rounded input and weights rounded to the compute type",
+           "slab": desc}
+    err.update(slab_errors(cfg, gpu, ref, planes) or {})
+    if code != 0:
+        _, _, _, _, ref_u = oracle_sample(cfg, inputs, planes=planes, rounded=False, keep=True)
+        eu = slab_errors(cfg, gpu, ref_u, planes) or {}
+        err["rel_linf_vs_unrounded_draw"] = eu.get("rel_linf")
+        err["rel_l2_vs_unrounded_draw"] = eu.get("rel_l2")
+    return base, err
 
 
 def run_reference(args, cfg, world, rank):
@@ -266,7 +362,7 @@ def run_reference(args, cfg, world, rank):
     planes = oracle_sample_planes(cfg, budget_each, inputs)
     rates = []
     for i in range(args.warmup + args.steps):
-        rate, cores, desc, dt = oracle_sample(cfg, inputs, planes=planes)
+        rate, cores, desc, dt, _ = oracle_sample(cfg, inputs, planes=planes)
         if i == 0 and dt < 0.6 * budget_each and planes < cfg["dims"][0]:
             # the small probe overstates the per-plane cost: rescale once
             planes = int(min(cfg["dims"][0], planes * budget_each / max(dt, 0.05)))
@@ -496,23 +592,25 @@ def main():
     host = make_input(cfg, inputs, so2dr, torch)
     if args.sweep:
         return run_sweep(args, cfg, coeffs, host, hbm_peak, rank)
+    # the host link of this machine, measured in this process before the timed
+    # region: copy engines, 1 GiB per direction, each alone and both at once
+    link = so2dr.measure_link(1 << 30, sm_ctas=64, repeats=3)
+    torch.cuda.synchronize()
     tuned = None
     if args.tune > 0:
         # the timings do not depend on the values: the benchmark grid is the scratch
-        table, link = so2dr.autotune(cfg["dims"], cfg["r"], cfg.get("kind", "star"), coeffs, cfg["T"], cfg["budget"], cfg["dtype"],
-                                     scratch=host, max_candidates=args.tune, repeats=2,
-                                     min_chunks=cfg["min_chunks"], k_on=cfg["k_on"] if args.k_on else 0,
-                                     k_off=cfg["k_off"] if args.k_off else 0)
-        tuned = {"candidates_timed": args.tune, "link_gbs": {"h2d": link[0], "d2h": link[1], "hbm": link[2]},
+        table, tl = so2dr.autotune(cfg["dims"], cfg["r"], cfg.get("kind", "star"), coeffs, cfg["T"], cfg["budget"],
+                                   cfg["dtype"], scratch=host, max_candidates=args.tune, repeats=2,
+                                   min_chunks=cfg["min_chunks"], k_on=cfg["k_on"] if args.k_on else 0,
+                                   k_off=cfg["k_off"] if args.k_off else 0)
+        tuned = {"candidates_timed": args.tune, "link_gbs": {"h2d": tl[0], "d2h": tl[1], "hbm": tl[2]},
                  "table": [[e["k_off"], e["k_on"], e["chunks"], e["lookahead"], e["out_slabs"],
                             round(e["predicted_ms"], 2), round(e["measured_ms"], 2)] for e in table[:args.tune]],
                  "columns": ["k_off", "k_on", "chunks", "lookahead", "out_slabs", "predicted_ms", "measured_ms"]}
         plan = so2dr.Plan(cfg["dims"], cfg["r"], cfg.get("kind", "star"), coeffs, cfg["T"], budget_bytes=cfg["budget"],
                           dtype=cfg["dtype"], tune_entry=table[0])
     else:
-        plan = so2dr.Plan(cfg["dims"], cfg["r"], cfg.get("kind", "star"), coeffs, cfg["T"], min_chunks=cfg["min_chunks"],
-                          k_on=cfg["k_on"], k_off=cfg["k_off"], budget_bytes=cfg["budget"], dtype=cfg["dtype"],
-                          link_gbs=(LINK_BIDIR_GBS / 2, LINK_BIDIR_GBS / 2), hbm_gbs=hbm_peak)
+        plan = make_plan(cfg, coeffs, so2dr)
     info = plan.info
     mode = {"so2dr": 0, "incore": 1, "resreu": 2}[args.mode]
     plan.bind(in_core=mode)
@@ -548,13 +646,6 @@ def main():
     mk_ms = sum(s["main_kernel_ms"] for s in stats)
     mk_n = sum(s["main_kernel_launches"] for s in stats)
     mk_cells = sum(s["main_kernel_cells"] for s in stats)
-    # (input + output) plane bytes of the k_on-deep launches of one run
-    io_bytes = 0.0
-    n_main = 0
-    for o in plan.ops():
-        if o["kind"] == 1 and o["depth"] == info["k_on"]:
-            io_bytes += ((o["src_hi"] - o["src_lo"]) + (o["dst_hi"] - o["dst_lo"])) * info["plane_bytes"]
-            n_main += 1
     b = {"f64": 8, "f32": 4, "bf16": 2, "f16": 2}[cfg["dtype"]]
     alg_bytes_per_launch = 2 * b * mk_cells / max(1, mk_n)
     avg_launch_s = mk_ms / max(1, mk_n) * 1e-3
@@ -566,16 +657,25 @@ def main():
     alg_flops_per_launch = (2 * npts - 1) * depth * mk_cells / max(1, mk_n)
     achieved_tf = alg_flops_per_launch / avg_launch_s / 1e12 if mk_n else 0.0
     alu_bound = alg_flops_per_launch / (ALU_PEAK_TFLOPS * 1e12) > alg_bytes_per_launch / (hbm_peak * 1e9)
-    # whole-path roofline: max(host-link time, HBM time) of the algorithmic bytes
-    R, L = info["rounds"], -(-info["k_off"] // info["k_on"])
-    Nb = 1
+    kind = cfg.get("kind", "star")
+    traffic = DRAM_TRAFFIC.get(source_digest(KERNEL_SRC[kind]), {}).get(args.config) if mode == 0 else None
+    # whole-path roofline: max(host-link time, HBM time) of the algorithmic
+    # bytes (every cell sent and received once per round; two HBM passes for
+    # the transfers and two per fused launch), against the link measured above
+    t_meas = dev_ms / args.steps * 1e-3
+    Nb = b
     for e in cfg["dims"]:
         Nb *= e
-    Nb *= b
-    b_host = 2.0 * Nb * R
-    b_hbm = Nb * R * (2.0 + 2.0 * L)
-    t_roof = max(b_host / (LINK_BIDIR_GBS * 1e9), b_hbm / (hbm_peak * 1e9))
-    t_meas = dev_ms / args.steps * 1e-3
+    pr = path_roofline(Nb, info["rounds"], -(-info["k_off"] // info["k_on"]), link, hbm_peak)
+    # the same against the fewest rounds the budget admits (largest feasible
+    # k_off), so that plans with different round counts read on one scale
+    cand = so2dr.candidates(cfg["dims"], cfg["r"], kind, coeffs, cfg["T"], min_chunks=cfg["min_chunks"],
+                            budget_bytes=cfg["budget"], dtype=cfg["dtype"])
+    kmax = max(c["k_off"] for c in cand)
+    konmax = max(c["k_on"] for c in cand if c["k_off"] == kmax)
+    rmin = -(-cfg["T"] // kmax)
+    prm = path_roofline(Nb, rmin, -(-kmax // konmax), link, hbm_peak)
+    t_pool = max(2.0 * Nb * info["rounds"] / (LINK_BIDIR_GBS * 1e9), pr["t_hbm_s"])
     h2d = stats[-1]["h2d_bytes"]
     d2h = stats[-1]["d2h_bytes"]
     line = {
@@ -586,18 +686,22 @@ def main():
         "config": {"workload": cfg["workload"], "mode": args.mode, "dims": list(cfg["dims"]), "radius": cfg["r"],
                    "time_steps": cfg["T"], "device_budget_bytes": cfg["budget"], "k_off": info["k_off"],
                    "k_on": info["k_on"] if mode != 2 else 1,
-                   "chunks": info["chunks"] if mode != 2 else info["result_reuse_chunks"], "rounds": R,
+                   "chunks": info["chunks"] if mode != 2 else info["result_reuse_chunks"], "rounds": info["rounds"],
                    "ring_planes": info["ring_planes"], "arena_bytes": info["arena_bytes"],
                    "lookahead": info["lookahead"], "out_slabs": info["out_slabs"],
-                   "redundancy": info["redundancy"], "parallelism": "replicas" if world > 1 else "1 GPU",
+                   "redundancy": info["redundancy"], "plan": "given k_off/k_on" if (cfg["k_off"] or cfg["k_on"])
+                   else "the planner's automatic choice",
+                   "parallelism": "replicas" if world > 1 else "1 GPU",
                    "l2": "inputs larger than L2 (grid of %.1f GiB vs 126 MB L2)" % (Nb / 2 ** 30)},
-        "path_roofline": {"bound": "host-link" if b_host / LINK_BIDIR_GBS >= b_hbm / hbm_peak else "hbm",
-                          "t_roof_ms": t_roof * 1e3, "t_measured_ms": t_meas * 1e3, "frac": t_roof / t_meas,
-                          "host_bytes": b_host, "hbm_bytes": b_hbm, "link_bidir_gbs": LINK_BIDIR_GBS,
-                          "hbm_gbs": hbm_peak,
-                          "measured_link_gbs": {"h2d": h2d / (stats[-1]["h2d_ms"] * 1e-3) / 1e9,
-                                                "d2h": d2h / (stats[-1]["d2h_ms"] * 1e-3) / 1e9,
-                                                "both_during_run": (h2d + d2h) / (stats[-1]["total_ms"] * 1e-3) / 1e9}},
+        "path_roofline": {"bound": pr["bound"], "t_roof_ms": pr["t_roof_s"] * 1e3, "t_measured_ms": t_meas * 1e3,
+                          "frac": pr["t_roof_s"] / t_meas, "frac_vs_measured_link": pr["t_roof_s"] / t_meas,
+                          "link_measured_gbs": {k: link[k] for k in ("ce_h2d", "ce_d2h", "ce_both_h2d",
+                                                                     "ce_both_d2h")},
+                          "frac_min_rounds": prm["t_roof_s"] / t_meas, "min_rounds": rmin, "k_off_max": kmax,
+                          "frac_vs_pool_link": t_pool / t_meas, "link_pool_bidir_gbs": LINK_BIDIR_GBS,
+                          "host_bytes": 2.0 * Nb * info["rounds"], "hbm_bytes": pr["hbm_bytes"], "hbm_gbs": hbm_peak,
+                          "stream_gbs_during_run": {"h2d": h2d / (stats[-1]["h2d_ms"] * 1e-3) / 1e9,
+                                                    "d2h": d2h / (stats[-1]["d2h_ms"] * 1e-3) / 1e9}},
         "roofline": {"bound": "alu" if alu_bound else "hbm",
                      "achieved": achieved_tf if alu_bound else achieved,
                      "peak": ALU_PEAK_TFLOPS if alu_bound else hbm_peak,
@@ -606,12 +710,11 @@ def main():
                      "hbm": {"achieved_gbs": achieved, "peak_gbs": hbm_peak, "frac": achieved / hbm_peak},
                      "alu": {"achieved_tflops": achieved_tf, "peak_tflops": ALU_PEAK_TFLOPS,
                              "frac": achieved_tf / ALU_PEAK_TFLOPS, "flop_per_cell_step": 2 * npts - 1},
-                     "traffic": (DRAM_PER_ALG_BYTE_R1K4_F32 * io_bytes / max(1, n_main)
-                                 if (cfg.get("kind", "star"), len(cfg["dims"]), cfg["r"], info["k_on"],
-                                     cfg["dtype"]) == ("star", 3, 1, 4, "f32") else None),
-                     "kernel": ("box2d_fast_kernel" if cfg.get("kind") == "box" else "star3d_fast_kernel")
+                     "traffic": traffic,
+                     "kernel": ("box2d_fast_kernel" if kind == "box" else "star3d_tb_kernel")
                                + " (k_on-step TB launch)", "peak_kind": ("derived from unit counts and the maximum SM clock" if alu_bound
                                    else peak_kind + " (burst)"),
+                     "alg_bytes_per_launch": alg_bytes_per_launch,
                      "avg_launch_ms": avg_launch_s * 1e3, "launches": mk_n},
         "e2e": {"value": e2e, "unit": "Gcell/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": int(sum(s["launches"] for s in stats)),
@@ -626,17 +729,7 @@ def main():
         with open(args.timeline, "w") as f:
             json.dump(plan.timeline(in_core=mode), f)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        from paper_2309_08864_gb300 import inputs as _inp
-        import oracle
-        oracle.build.build()
-        planes = oracle_sample_planes(cfg, 15.0, _inp)
-        rate, cores, desc, dt = oracle_sample(cfg, _inp, planes=planes)
-        if dt < 10.0 and planes < cfg["dims"][0]:
-            # the small probe overstates the per-plane cost: rescale once
-            planes = int(min(cfg["dims"][0], planes * 15.0 / max(dt, 0.05)))
-            rate, cores, desc, dt = oracle_sample(cfg, _inp, planes=planes)
-        line["cpu_baseline"] = {"value": rate / 1e9, "unit": "Gcell/s", "cores": cores, "kind": "oracle",
-                                "sample": desc + " (%.1f s)" % dt}
+        line["cpu_baseline"], line["error_vs_oracle"] = cpu_baseline_leg(cfg, plan, mode, torch, inputs, so2dr)
     plan.close()
     if rank == 0:
         print(json.dumps(line), flush=True)

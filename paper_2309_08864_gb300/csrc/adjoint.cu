@@ -114,14 +114,16 @@ __device__ __forceinline__ double block_sum(double v) {
     return r;
 }
 
-// lambda = u - target on owned planes; FP64 partial sums of lambda^2
+// lambda = u - target on owned planes; FP64 partial sums of (u - target)^2,
+// the difference formed in FP64
 template <typename T>
 __global__ void __launch_bounds__(256) residual_kernel(const T* u, const T* tg, T* lam, int64_t n, double* partial) {
     double acc = 0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        T d = u[i] - tg[i];
-        if (lam) lam[i] = d;
-        acc += (double)d * (double)d;
+        // lambda_T in the storage precision; the loss from the FP64 difference
+        if (lam) lam[i] = u[i] - tg[i];
+        const double d = (double)u[i] - (double)tg[i];
+        acc = fma(d, d, acc);
     }
     double b = block_sum(acc);
     if (threadIdx.x == 0) partial[blockIdx.x] = b;

@@ -147,13 +147,16 @@ int stencil_occupancy(int dtype, int shape, int r, int depth, const LaunchShape&
 
 int choose_segments(int64_t tiles, int64_t nout, int r, int depth, int sms, int occ) {
     if (tiles <= 0 || nout <= 0 || sms <= 0) return 1;
-    int64_t slots = (int64_t)sms * (occ > 0 ? occ : 1);
+    (void)occ;
     int best = 1;
     double best_cost = 0;
     for (int n = 1; n <= 64 && n <= nout; ++n) {
-        int64_t waves = (tiles * n + slots - 1) / slots;
-        double len = (double)nout / n + 2.0 * r * depth + depth;  // planes one CTA streams
-        double cost = (double)waves * len;
+        // the CTAs resident on one SM share its throughput, so an SM's time
+        // goes with the CTAs it receives (the busiest SM gets
+        // ceil(tiles * n / sms)) times the planes each streams
+        int64_t per_sm = (tiles * n + sms - 1) / sms;
+        double len = (double)nout / n + 2.0 * r * depth + depth;
+        double cost = (double)per_sm * len;
         if (n == 1 || cost < best_cost * 0.98) { best = n; best_cost = cost; }
     }
     return best;

@@ -50,7 +50,9 @@ cudaError_t launch_stencil(int dtype, int shape, int r, const StencilArgs& a, co
 int stencil_occupancy(int dtype, int shape, int r, int depth, const LaunchShape& ls);
 
 // Axis-0 segments for a launch with `tiles` CTAs per segment, nout output
-// planes and halo r*depth: the count that minimises waves x stream length.
+// planes and halo r*depth: the count that minimises the CTAs the busiest SM
+// receives times the planes each streams (occ: CTAs per SM, unused: resident
+// CTAs share the SM's throughput).
 int choose_segments(int64_t tiles, int64_t nout, int r, int depth, int sms, int occ);
 
 // Per-dtype instantiations (one translation unit each).

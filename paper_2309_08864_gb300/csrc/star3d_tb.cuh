@@ -17,17 +17,21 @@
 //    slot of a target is fixed by its plane index modulo 2R and the plane
 //    loop is unrolled 2R times, so the ring never moves data;
 //  * levels are pipelined across planes: level L consumes what level L-1
-//    completed in the previous phase (two shared-memory plane slots per
-//    level), so one barrier per plane suffices; y neighbours come from
-//    shared memory, x neighbours from warp shuffles;
+//    completed in the previous phase, so one barrier per plane suffices.  A
+//    thread's own cells of that plane stay in its registers (levels run from
+//    the deepest down, so each reads them before they are replaced); only
+//    the R rows at each end of a warp's rows go to shared memory (two plane
+//    slots per level), for the neighbouring warps.  x neighbours come from
+//    warp shuffles;
 //  * every cell is computed as if interior.  Cells of the fixed boundary
 //    (the in-plane ring of width R and the first and last R planes) keep
-//    their value: in warps or planes that hold such cells, the centre
-//    arrival of a boundary target stores the arriving value and the later
-//    arrivals leave it alone (per-cell selects on a slower path that only
-//    boundary warps and edge planes take);
-//  * phases in which every level is active and no boundary plane is in
-//    flight run a straight-line body without per-level tests.
+//    their value: the centre arrival of a boundary target stores the
+//    arriving value and the later arrivals leave it alone.  Warps whose only
+//    boundary cells are the ring's columns select those cells by a per-lane
+//    predicate; warps with boundary rows, and phases with a fixed plane in
+//    flight, select per cell on a slower path;
+//  * phases in which every level is active and no fixed plane is in flight
+//    run a straight-line body without per-level tests.
 // The valid area shrinks by R per level in y and x: the compute-area
 // adjustment of Algorithm 1 applied inside a launch.
 //
@@ -42,14 +46,14 @@
 
 namespace so2dr {
 
-// Tile shape per (R, K): 16 warps of 2 rows for fused depths (8 warps for one
-// level, where no y halo is lost and several CTAs share an SM).  Four fused
-// levels of radius 1 keep 64 partial sums per thread, which fits a 512-thread
-// CTA in the register file.
+// Tile shape per (R, K).  Fused depths: 8 warps of 4 rows, whose partial sums
+// (K * 2R * 16 per thread) and carried cells fit the 255-register limit of a
+// 256-thread CTA.  One level: 8 warps of 2 rows, two CTAs per SM.
 template <int R, int K> struct StarShape {
-    static constexpr int VY = 2;
-    static constexpr int NW = K == 1 ? 8 : 16;
+    static constexpr int VY = K == 1 ? 2 : 4;
+    static constexpr int NW = 8;
     static constexpr int NT = NW * 32;
+    static constexpr bool CARRY = K > 1;                // own cells of a level stay in registers
     static constexpr int LX = 128;                      // tile columns (32 lanes x 4)
     static constexpr int LYT = NW * VY;                 // tile rows
     static constexpr int HXA = ((R * K + 3) / 4) * 4;   // x halo, whole 4-cell vectors
@@ -73,6 +77,13 @@ template <int R, int K> struct StarShape {
     }
 };
 
+// How a warp treats the fixed boundary in a phase.
+enum BndMode : int {
+    kBndNone = 0,     // no boundary cell in the warp, no fixed plane in flight
+    kBndColumns = 1,  // only the ring's columns: lanes holding column 0 or nx-1 select
+    kBndCells = 2,    // boundary rows or fixed planes: per-cell masks
+};
+
 template <typename T, int R, int K>
 struct StarTB {
     using S = StarShape<R, K>;
@@ -91,11 +102,14 @@ struct StarTB {
     int za, zb, olo, ohi, need_lo, need_hi;
     int ps_lo, ps_hi;     // phases in which every level is active
     int pfail;            // phase whose input copy did not land in time
+    int wmode;            // BndMode of my warp away from the fixed planes
     int64_t plane;
-    bool xin, warp_bnd;
+    bool xin;
+    bool xl, xr;          // my lane holds column 0 / column nx-1 of the grid
     unsigned inyx;        // bit y*4+e: my cell (row y, column e) is interior in its plane
     T* out;
-    float2 A[K][W2][VY][2];  // 2R partial sums per cell per level, in x pairs
+    float2 A[K][W2][VY][2];                 // 2R partial sums per cell per level, in x pairs
+    float2 C[K > 1 ? K - 1 : 1][VY][2];     // my cells of what levels 0..K-2 completed last phase
 
     __device__ __forceinline__ explicit StarTB(const StencilArgs& args, const CUtensorMap* m) : a(args), tmap(m) {}
 
@@ -107,7 +121,7 @@ struct StarTB {
     __device__ __forceinline__ int lev_hi(int L) const { return need_hi + (K - L) * R; }
 
     // boundary mask (bits y*4+e) of target plane zt: every cell of a fixed
-    // plane, else the in-plane ring
+    // plane, else the in-plane ring (and the cells outside the grid)
     __device__ __forceinline__ unsigned bmask(int zt) const {
         return (zt < R || zt >= n0 - R) ? kAll : (~inyx & kAll);
     }
@@ -122,15 +136,29 @@ struct StarTB {
         tma_load_3d(sin0 + (uint32_t)(q % NI) * SLOT, tmap, bx0, ys - R, slot, bar);
     }
 
-    __device__ __forceinline__ static float2 sel2(unsigned m, int bit, float2 keep, float2 nv) {
-        return make_float2(((m >> bit) & 1u) ? keep.x : nv.x, ((m >> (bit + 1)) & 1u) ? keep.y : nv.y);
+    // keep (boundary) or nv, per element of a pair: per-cell mask bits
+    // (kBndCells) or the column predicates of my lane (kBndColumns)
+    template <int MODE>
+    __device__ __forceinline__ float2 pick(unsigned m, int y, int h, float2 keep, float2 nv) const {
+        const int e0 = 2 * h, bit = 4 * y + e0;
+        if constexpr (MODE == kBndCells) {
+            return make_float2(((m >> bit) & 1u) ? keep.x : nv.x, ((m >> (bit + 1)) & 1u) ? keep.y : nv.y);
+        } else if constexpr (MODE == kBndColumns) {
+            // columns 0..R-1 are cells e < R of the lane holding column 0,
+            // columns nx-R..nx-1 cells e >= 4-R of the lane holding nx-1
+            const bool p0 = (e0 < R && xl) || (e0 >= 4 - R && xr);
+            const bool p1 = (e0 + 1 < R && xl) || (e0 + 1 >= 4 - R && xr);
+            return make_float2(p0 ? keep.x : nv.x, p1 ? keep.y : nv.y);
+        } else {
+            return nv;
+        }
     }
 
     // One arrival at level L whose target phase is PHL = (zp - za) mod 2R:
     // v holds my cells of the arriving plane, `rows` its shared-memory copy
-    // (tile row t at row t + R, my first column at element col).  Boundary
-    // masks mz[t] (t = 0..R) belong to targets zp - R + t (BND only).
-    template <int L, int PHL, bool BND, typename ST>
+    // (tile row t at row t + R, my first column at element col).  Masks
+    // mz[t] (t = 0..R, kBndCells only) belong to targets zp - R + t.
+    template <int L, int PHL, int MODE, typename ST>
     __device__ __forceinline__ void arrive(const float2 (&v)[VY][2], const ST* rows, int pitch, int col,
                                            float2 (&done)[VY][2], const unsigned (&mz)[R + 1]) {
         // x neighbours beyond my 4 cells, from the adjacent lanes
@@ -173,7 +201,7 @@ struct StarTB {
         for (int y = 0; y < VY; ++y)
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
-                const int e0 = 2 * h, bit = 4 * y + 2 * h;
+                const int e0 = 2 * h;
                 const float2 x = v[y][h];
 #pragma unroll
                 for (int t = R + 1; t < 2 * R; ++t) {
@@ -194,17 +222,15 @@ struct StarTB {
                         s2 = __ffma2_rn(a.cf2[cidx<R>(2, +1, j)], xpair(y, e0 + j), s2);
                     }
                     // a boundary target keeps the value of its centre arrival
-                    acc = BND ? sel2(mz[R], bit, x, s2) : s2;
+                    acc = pick<MODE>(mz[R], y, h, x, s2);
                 }
 #pragma unroll
                 for (int t = 1; t < R; ++t) {
                     float2& acc = A[L][pmod(PHL - R + t, W2)][y][h];
-                    const float2 nv = __ffma2_rn(a.cf2[cidx<R>(0, +1, R - t)], x, acc);
-                    acc = BND ? sel2(mz[t], bit, acc, nv) : nv;
+                    acc = pick<MODE>(mz[t], y, h, acc, __ffma2_rn(a.cf2[cidx<R>(0, +1, R - t)], x, acc));
                 }
                 float2& a0 = A[L][pmod(PHL - R, W2)][y][h];
-                const float2 fin = __ffma2_rn(a.cf2[cidx<R>(0, +1, R)], x, a0);
-                done[y][h] = BND ? sel2(mz[0], bit, a0, fin) : fin;
+                done[y][h] = pick<MODE>(mz[0], y, h, a0, __ffma2_rn(a.cf2[cidx<R>(0, +1, R)], x, a0));
                 a0 = __fmul2_rn(a.cf2[cidx<R>(0, -1, R)], x);  // first contribution to target zp + R
             }
     }
@@ -225,12 +251,12 @@ struct StarTB {
     // level L of phase p (PH = p mod 2R; p0 is a multiple of 2R, so the
     // parity of p is that of PH): consumes input plane za + p (L = 0) or what
     // level L-1 completed in phase p-1 (plane za + p - L(R+1))
-    template <int L, int PH, bool BND>
+    template <int L, int PH, int MODE>
     __device__ __forceinline__ void level_body(int p) {
         const int zp = za + p - L * (R + 1);
         unsigned mz[R + 1];
 #pragma unroll
-        for (int t = 0; t <= R; ++t) mz[t] = BND ? bmask(zp - R + t) : 0u;
+        for (int t = 0; t <= R; ++t) mz[t] = MODE == kBndCells ? bmask(zp - R + t) : 0u;
         float2 v[VY][2], done[VY][2];
         constexpr int PHL = pmod(PH - L * (R + 1), W2);
         if constexpr (L == 0) {
@@ -241,44 +267,59 @@ struct StarTB {
                 v[y][0] = make_float2(q.x, q.y);
                 v[y][1] = make_float2(q.z, q.w);
             }
-            arrive<0, PHL, BND>(v, rows, LXB, col0, done, mz);
+            arrive<0, PHL, MODE>(v, rows, LXB, col0, done, mz);
         } else {
             const float* prev = slev + ((L - 1) * NB + ((PH + 1) & 1)) * ROWS * LX;  // slot of phase p-1
 #pragma unroll
             for (int y = 0; y < VY; ++y) {
-                const float4 q = lds4(prev + (my_row + y + R) * LX + lane * 4);
-                v[y][0] = make_float2(q.x, q.y);
-                v[y][1] = make_float2(q.z, q.w);
+                if constexpr (S::CARRY) {
+                    v[y][0] = C[L - 1][y][0];
+                    v[y][1] = C[L - 1][y][1];
+                } else {
+                    const float4 q = lds4(prev + (my_row + y + R) * LX + lane * 4);
+                    v[y][0] = make_float2(q.x, q.y);
+                    v[y][1] = make_float2(q.z, q.w);
+                }
             }
-            arrive<L, PHL, BND>(v, prev, LX, lane * 4, done, mz);
+            arrive<L, PHL, MODE>(v, prev, LX, lane * 4, done, mz);
         }
         if constexpr (L == K - 1) {
             emit(done, zp - R);
         } else {
+            // my cells stay in registers for level L+1; the shared-memory plane
+            // serves the neighbouring warps (the R rows at each end)
             float* lb = slev + (L * NB + (PH & 1)) * ROWS * LX;
 #pragma unroll
-            for (int y = 0; y < VY; ++y)
-                *reinterpret_cast<float4*>(lb + (my_row + y + R) * LX + lane * 4) =
-                    make_float4(done[y][0].x, done[y][0].y, done[y][1].x, done[y][1].y);
+            for (int y = 0; y < VY; ++y) {
+                if (!S::CARRY || y < R || y >= VY - R)
+                    *reinterpret_cast<float4*>(lb + (my_row + y + R) * LX + lane * 4) =
+                        make_float4(done[y][0].x, done[y][0].y, done[y][1].x, done[y][1].y);
+                if constexpr (S::CARRY) {
+                    C[L][y][0] = done[y][0];
+                    C[L][y][1] = done[y][1];
+                }
+            }
         }
     }
 
-    // every level active, no boundary cell or plane in flight
-    template <int L, int PH>
-    __device__ __forceinline__ void levels_fast(int p) {
-        level_body<L, PH, false>(p);
-        if constexpr (L + 1 < K) levels_fast<L + 1, PH>(p);
+    // every level active, no fixed plane in flight; levels run from the
+    // deepest down, so that level L reads the carried cells of level L-1
+    // before level L-1 replaces them
+    template <int L, int PH, int MODE>
+    __device__ __forceinline__ void levels_steady(int p) {
+        level_body<L, PH, MODE>(p);
+        if constexpr (L > 0) levels_steady<L - 1, PH, MODE>(p);
     }
 
-    // head and tail of the stream, edge planes and boundary warps
+    // head and tail of the stream, and the fixed planes
     template <int L, int PH>
     __device__ __forceinline__ void levels_checked(int p) {
         const int zp = za + p - L * (R + 1);
         if (zp >= lev_lo(L) && zp < lev_hi(L)) {
-            if (warp_bnd || zp < 2 * R || zp >= n0 - R) level_body<L, PH, true>(p);
-            else level_body<L, PH, false>(p);
+            if (wmode == kBndNone && zp >= 2 * R && zp < n0 - R) level_body<L, PH, kBndNone>(p);
+            else level_body<L, PH, kBndCells>(p);
         }
-        if constexpr (L + 1 < K) levels_checked<L + 1, PH>(p);
+        if constexpr (L > 0) levels_checked<L - 1, PH>(p);
     }
 
     // phase p = p0 + PH; false when an input copy did not land in time
@@ -296,9 +337,12 @@ struct StarTB {
             fence_proxy_async_smem();
             issue(p + PD);
         }
-        const int zmin = za + p - (K - 1) * (R + 1), zmax = za + p;
-        if (p >= ps_lo && p < ps_hi && !warp_bnd && zmin >= 2 * R && zmax < n0 - R) levels_fast<0, PH>(p);
-        else levels_checked<0, PH>(p);
+        // the arrivals of this phase span planes za + p - (K-1)(R+1) .. za + p;
+        // a fixed plane among their targets (z' - R .. z') needs the cell path
+        const bool steady = p >= ps_lo && p < ps_hi && za + p - (K - 1) * (R + 1) >= 2 * R && za + p < n0 - R;
+        if (steady && wmode == kBndNone) levels_steady<K - 1, PH, kBndNone>(p);
+        else if (steady && wmode == kBndColumns) levels_steady<K - 1, PH, kBndColumns>(p);
+        else levels_checked<K - 1, PH>(p);
         if constexpr (PH + 1 < W2) return phase<PH + 1>(p0);
         return true;
     }
@@ -331,7 +375,20 @@ struct StarTB {
                 const int gy = ys + my_row + y, gx = gx0 + e;
                 if (gy >= R && gy < ny - R && gx >= R && gx < nx - R) inyx |= 1u << (y * 4 + e);
             }
-        warp_bnd = __any_sync(0xffffffffu, inyx != kAll);
+        // boundary mode of my warp: rows of the ring (or a lane holding both
+        // ring sides) need per-cell masks; the ring's columns alone, a lane
+        // predicate (R <= 4 columns, all inside the 4 cells of one lane)
+        bool brow = false;
+#pragma unroll
+        for (int y = 0; y < VY; ++y) {
+            const int gy = ys + my_row + y;
+            brow |= (gy >= 0 && gy < R) || (gy >= ny - R && gy < ny);
+        }
+        xl = gx0 == 0;
+        xr = gx0 == nx - 4;
+        if (__any_sync(0xffffffffu, brow || (xl && xr))) wmode = kBndCells;
+        else if (__any_sync(0xffffffffu, xl || xr)) wmode = kBndColumns;
+        else wmode = kBndNone;
 #pragma unroll
         for (int l = 0; l < K; ++l)
 #pragma unroll
@@ -340,6 +397,12 @@ struct StarTB {
                 for (int y = 0; y < VY; ++y)
 #pragma unroll
                     for (int h = 0; h < 2; ++h) A[l][q][y][h] = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int l = 0; l < (K > 1 ? K - 1 : 1); ++l)
+#pragma unroll
+            for (int y = 0; y < VY; ++y)
+#pragma unroll
+                for (int h = 0; h < 2; ++h) C[l][y][h] = make_float2(0.f, 0.f);
         // axis-0 segment of this CTA: outputs [zs, ze), stream over [za, zb)
         const int nseg = gridDim.z;
         const int nout = (int)(a.out_hi - a.out_lo), in_lo = (int)a.in_lo, in_hi = (int)a.in_hi;

@@ -15,21 +15,28 @@ pytestmark = pytest.mark.gpu
 C2 = dict(dims=(1024, 1024, 1024), r=1, coeffs=[0.4] + [0.1] * 6, T=64, budget=1 << 30, min_chunks=8)
 
 
-def sample_boxes(dims, chunk_starts, rng, n_random=3, w=4):
-    """Corners, chunk boundaries and random spots."""
+def sample_boxes(dims, chunk_starts, rng, n_random=3, w=4, every_boundary=False):
+    """Corners, chunk boundaries (every one, on both sides, or a quarter of
+    them) and random spots."""
     boxes = [((0, 0, 0)), tuple(d - w for d in dims)]
-    for s in chunk_starts[1:-1][:: max(1, len(chunk_starts) // 4)]:
-        boxes.append((max(0, s - w // 2), int(rng.integers(0, dims[1] - w)), dims[2] - w))
+    inner = chunk_starts[1:-1]
+    if every_boundary:
+        for s in inner:
+            for z in (max(0, s - w), min(dims[0] - w, s)):
+                boxes.append((z, int(rng.integers(0, dims[1] - w)), int(rng.integers(0, dims[2] - w))))
+    else:
+        for s in inner[:: max(1, len(chunk_starts) // 4)]:
+            boxes.append((max(0, s - w // 2), int(rng.integers(0, dims[1] - w)), dims[2] - w))
     for _ in range(n_random):
         boxes.append(tuple(int(rng.integers(0, d - w)) for d in dims))
     return [(lo, tuple(l + w for l in lo)) for lo in boxes]
 
 
-def cone_check(dims, r, coeffs, T, dtype, host_after, starts, tol, seed=1, n_random=3):
+def cone_check(dims, r, coeffs, T, dtype, host_after, starts, tol, seed=1, n_random=3, every_boundary=False):
     rng = np.random.default_rng(0)
     errs = []
     c_ref = gu.compute_coeffs(coeffs, dtype)
-    for lo, hi in sample_boxes(dims, starts, rng, n_random):
+    for lo, hi in sample_boxes(dims, starts, rng, n_random, every_boundary=every_boundary):
         blo, bhi = oracle.cone_box(dims, lo, hi, r * T)
         ub = inputs.to_storage(inputs.draw_box(seed, dims, blo, bhi), dtype)
         ref = oracle.run_cone(inputs.storage_to_f64(ub, dtype), c_ref, r, oracle.STAR, T, blo, bhi, dims, lo, hi)
@@ -38,17 +45,19 @@ def cone_check(dims, r, coeffs, T, dtype, host_after, starts, tol, seed=1, n_ran
         e = float(np.max(np.abs(got - ref)) / np.max(np.abs(ref)))
         errs.append(e)
         assert e <= tol, (lo, e)
-    return max(errs)
+    return max(errs), len(errs)
 
 
-def _full_run(dims, r, coeffs, T, dtype, budget, min_chunks, k_on=0, k_off=0, in_core_check=True, seed=1):
+def _full_run(dims, r, coeffs, T, dtype, budget, min_chunks, k_on=0, k_off=0, in_core_check=True, seed=1,
+              plan=None):
     import torch
     u = inputs.draw_box(seed, dims, as_f32=True)
     st = inputs.to_storage(u, dtype) if dtype != so2dr.F32 else u
     host = gu.pinned_from_storage(st, dtype)
     ref_copy = host.clone().pin_memory() if in_core_check else None
-    plan = so2dr.Plan(dims, r, "star", coeffs, T, min_chunks=min_chunks, k_on=k_on, k_off=k_off,
-                      budget_bytes=budget, dtype=dtype, link_gbs=(171, 171), hbm_gbs=6781)
+    if plan is None:
+        plan = so2dr.Plan(dims, r, "star", coeffs, T, min_chunks=min_chunks, k_on=k_on, k_off=k_off,
+                          budget_bytes=budget, dtype=dtype)
     info = plan.info
     assert info["arena_bytes"] <= budget
     plan.run(host)
@@ -63,32 +72,52 @@ def _full_run(dims, r, coeffs, T, dtype, budget, min_chunks, k_on=0, k_off=0, in
     return host, starts, info
 
 
+def bench_plan(name):
+    """The plan bench.py times for one of its configs (same constructor)."""
+    import bench
+    cfg = dict(bench.CONFIGS[name])
+    return cfg, bench.coeffs_of(cfg["coeffs"], inputs), bench.make_plan(cfg, bench.coeffs_of(cfg["coeffs"], inputs),
+                                                                        so2dr)
+
+
 def test_c2_7pt_1024cubed_fp32_full_size():
-    d = C2
-    host, starts, info = _full_run(d["dims"], d["r"], d["coeffs"], d["T"], so2dr.F32, d["budget"], d["min_chunks"])
+    """The benchmarked plan of the 1024^3 7-point FP32 workload (64 steps,
+    1 GiB): out-of-core byte-identical to in-core, and the FP64 oracle on
+    dependency cones on both sides of every chunk boundary plus random spots."""
+    cfg, c, plan = bench_plan("c2")
+    dims = cfg["dims"]
+    host, starts, info = _full_run(dims, cfg["r"], c, cfg["T"], so2dr.F32, cfg["budget"], cfg["min_chunks"],
+                                   plan=plan)
     assert info["chunks"] >= 8
-    cone_check(d["dims"], d["r"], d["coeffs"], d["T"], so2dr.F32, host, starts, 1e-5)
+    err, n = cone_check(dims, cfg["r"], c, cfg["T"], so2dr.F32, host, starts, 1e-5, n_random=8, every_boundary=True)
+    assert n == 2 + 2 * (len(starts) - 2) + 8
+    print("C2_PLAN k_off=%d k_on=%d chunks=%d cones=%d max_rel_err=%.3e" % (info["k_off"], info["k_on"],
+                                                                        info["chunks"], n, err))
 
 
 def test_c3_25pt_r4_1536cubed_fp32_full_size():
-    dims, r, T = (1536, 1536, 1536), 4, 32
-    c = inputs.radius4_star_coeffs()
-    host, starts, info = _full_run(dims, r, c, T, so2dr.F32, 4 << 30, 1, in_core_check=True)
-    cone_check(dims, r, c, T, so2dr.F32, host, starts, 1e-5, n_random=1)
+    cfg, c, plan = bench_plan("c3")
+    host, starts, info = _full_run(cfg["dims"], cfg["r"], c, cfg["T"], so2dr.F32, cfg["budget"], cfg["min_chunks"],
+                                   plan=plan)
+    err, n = cone_check(cfg["dims"], cfg["r"], c, cfg["T"], so2dr.F32, host, starts, 1e-5, n_random=2,
+                        every_boundary=True)
+    print("C3_PLAN k_off=%d k_on=%d chunks=%d cones=%d max_rel_err=%.3e" % (info["k_off"], info["k_on"],
+                                                                        info["chunks"], n, err))
 
 
 def test_c4_precision_forms_1024cubed_128_steps():
-    """Storage in FP32 / BF16 / FP16 with FP32 arithmetic, 1 GiB budget: the
-    error against the FP64 oracle (same rounded input) on sampled cones, and
-    out-of-core byte-identical to in-core for the 16-bit forms."""
+    """Storage in FP32 / BF16 / FP16 with FP32 arithmetic, 1 GiB budget, the
+    benchmarked plans: the error against the FP64 oracle (same rounded input)
+    on sampled cones, and out-of-core byte-identical to in-core for every
+    storage type."""
     import json
     import torch
     dims, r, T = (1024, 1024, 1024), 1, 128
     coeffs = [0.4] + [0.1] * 6
     report = {}
-    for dtype, tol, koff in ((so2dr.F32, 1e-5, 8), (so2dr.BF16, 3e-2, 16), (so2dr.F16, 5e-3, 16)):
-        host, starts, info = _full_run(dims, r, coeffs, T, dtype, 1 << 30, 8, k_on=4, k_off=koff,
-                                       in_core_check=(dtype == so2dr.BF16))
+    for dtype, tol, name in ((so2dr.F32, 1e-5, "c4-f32"), (so2dr.BF16, 3e-2, "c4-bf16"), (so2dr.F16, 5e-3, "c4-f16")):
+        _, _, plan = bench_plan(name)
+        host, starts, info = _full_run(dims, r, coeffs, T, dtype, 1 << 30, 8, plan=plan)
         rng = np.random.default_rng(0)
         errs, l2n, l2d, errs_u, l2n_u, l2d_u = [], 0.0, 0.0, [], 0.0, 0.0
         for lo, hi in sample_boxes(dims, starts, rng, n_random=0, w=2)[:3]:
