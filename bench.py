@@ -69,7 +69,7 @@ CONFIGS = {
                min_chunks=4, k_on=4, k_off=8, zero_ring=True),
     "c2": dict(workload="3D 7-point star FP32 1024^3 (4 GiB), 64 steps, 1 GiB budget",
                dims=(1024, 1024, 1024), r=1, coeffs="star7", T=64, dtype="f32", budget=1 << 30,
-               min_chunks=8, k_on=4, k_off=16),
+               min_chunks=8, k_on=0, k_off=0),
     "c3": dict(workload="3D 25-point star r=4 FP32 1536^3 (14.5 GB), 32 steps, 4 GiB budget",
                dims=(1536, 1536, 1536), r=4, coeffs="r4", T=32, dtype="f32", budget=4 << 30,
                min_chunks=1, k_on=0, k_off=0),
@@ -532,70 +532,17 @@ def run_sweep(args, cfg, coeffs, host, hbm_peak, rank):
     return 0
 
 
-def main():
-    ap = argparse.ArgumentParser()
-    ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
-    ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--impl", default="so2dr", choices=["so2dr", "reference"])
-    ap.add_argument("--config", default="c2", choices=sorted(CONFIGS))
-    ap.add_argument("--k-off", type=int, default=None)
-    ap.add_argument("--k-on", type=int, default=None)
-    ap.add_argument("--kernel-case", type=int, default=0)
-    ap.add_argument("--radius", type=int, default=1)
-    ap.add_argument("--kind", default="star", choices=["star", "box"], help="--kernel-case stencil (box: 2D n x n)")
-    ap.add_argument("--launches", type=int, default=2)
-    ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", default="so2dr", choices=["so2dr", "incore", "resreu"],
-                    help="so2dr: the out-of-core SO2DR pipeline (default); incore: the whole grid on the "
-                         "device, same launch depths, transfers outside the timed region; resreu: the "
-                         "redundancy-free out-of-core comparison code (single-step launches, region "
-                         "sharing of intermediate results)")
-    ap.add_argument("--tune", type=int, default=0,
-                    help="measured autotune before timing: time the model's N best plans (so2dr_autotune) "
-                         "and benchmark the fastest")
-    ap.add_argument("--sweep", default="",
-                    help="comma-separated k_off values: measured and predicted time of one run per k_off "
-                         "(the run-time tuning trade-off of Sec. V-B); prints one JSON line")
-    ap.add_argument("--timeline", default="",
-                    help="write the per-op timeline (so2dr_run_timeline) of the last timed run to this JSON file")
-    ap.add_argument("--link", action="store_true",
-                    help="measure the host link (copy engines vs SM-driven copies over the mapped pinned "
-                         "buffers, each direction and both at once) and HBM; prints one JSON line")
-    args = ap.parse_args()
-    cfg = dict(CONFIGS[args.config])
-    if args.k_off is not None:
-        cfg["k_off"] = args.k_off
-    if args.k_on is not None:
-        cfg["k_on"] = args.k_on
-    world, rank, local = dist_setup()
-    if args.impl == "reference":
-        return run_reference(args, cfg, world, rank)
-
-    import torch
-    from paper_2309_08864_gb300 import inputs, so2dr
-    torch.cuda.set_device(local)
-    if args.kernel_case:
-        return run_kernel_case(args)
-    if args.link:
-        rows = {}
-        for ctas in (32, 64, 152):
-            rows[ctas] = so2dr.measure_link(1 << 30, sm_ctas=ctas, repeats=3)
-        print(json.dumps({"link_gbs": rows, "bytes": 1 << 30, "note": "keys by SM-copy CTA count; ce_* are "
-                          "cudaMemcpyAsync, sm_* a copy kernel over the mapped pinned buffer"}), flush=True)
-        return 0
-    if cfg.get("adjoint"):
-        return run_adjoint(args, cfg, world, rank, local)
-
+def bench_config(args, cfg, name, world, rank, local, torch, inputs, so2dr, link=None):
+    """Times one configuration (warm-up runs, then args.steps timed runs of
+    so2dr_run) and returns its JSON line."""
     hbm_peak, peak_kind = measured_peaks()
     coeffs = coeffs_of(cfg["coeffs"], inputs)
     host = make_input(cfg, inputs, so2dr, torch)
-    if args.sweep:
-        return run_sweep(args, cfg, coeffs, host, hbm_peak, rank)
     # the host link of this box, measured in this process before the timed
     # region: copy engines, 1 GiB per direction, each alone and both at once
-    link = so2dr.measure_link(1 << 30, sm_ctas=64, repeats=3)
-    torch.cuda.synchronize()
+    if link is None:
+        link = so2dr.measure_link(1 << 30, sm_ctas=64, repeats=3)
+        torch.cuda.synchronize()
     tuned = None
     if args.tune > 0:
         # the timings do not depend on the values: the benchmark grid is the scratch
@@ -658,7 +605,7 @@ def main():
     achieved_tf = alg_flops_per_launch / avg_launch_s / 1e12 if mk_n else 0.0
     alu_bound = alg_flops_per_launch / (ALU_PEAK_TFLOPS * 1e12) > alg_bytes_per_launch / (hbm_peak * 1e9)
     kind = cfg.get("kind", "star")
-    traffic = DRAM_TRAFFIC.get(source_digest(KERNEL_SRC[kind]), {}).get(args.config) if mode == 0 else None
+    traffic = DRAM_TRAFFIC.get(source_digest(KERNEL_SRC[kind]), {}).get(name) if mode == 0 else None
     # whole-path roofline: max(host-link time, HBM time) of the algorithmic
     # bytes (every cell sent and received once per round; two HBM passes for
     # the transfers and two per fused launch), against the link measured above
@@ -731,6 +678,89 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"], line["error_vs_oracle"] = cpu_baseline_leg(cfg, plan, mode, torch, inputs, so2dr)
     plan.close()
+    del host
+    return line
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="so2dr", choices=["so2dr", "reference"])
+    ap.add_argument("--config", default="c2", choices=sorted(CONFIGS) + ["c4"])
+    ap.add_argument("--k-off", type=int, default=None)
+    ap.add_argument("--k-on", type=int, default=None)
+    ap.add_argument("--kernel-case", type=int, default=0)
+    ap.add_argument("--radius", type=int, default=1)
+    ap.add_argument("--kind", default="star", choices=["star", "box"], help="--kernel-case stencil (box: 2D n x n)")
+    ap.add_argument("--launches", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--mode", default="so2dr", choices=["so2dr", "incore", "resreu"],
+                    help="so2dr: the out-of-core SO2DR pipeline (default); incore: the whole grid on the "
+                         "device, same launch depths, transfers outside the timed region; resreu: the "
+                         "redundancy-free out-of-core comparison code (single-step launches, region "
+                         "sharing of intermediate results)")
+    ap.add_argument("--tune", type=int, default=0,
+                    help="measured autotune before timing: time the model's N best plans (so2dr_autotune) "
+                         "and benchmark the fastest")
+    ap.add_argument("--sweep", default="",
+                    help="comma-separated k_off values: measured and predicted time of one run per k_off "
+                         "(the run-time tuning trade-off of Sec. V-B); prints one JSON line")
+    ap.add_argument("--timeline", default="",
+                    help="write the per-op timeline (so2dr_run_timeline) of the last timed run to this JSON file")
+    ap.add_argument("--link", action="store_true",
+                    help="measure the host link (copy engines vs SM-driven copies over the mapped pinned "
+                         "buffers, each direction and both at once) and HBM; prints one JSON line")
+    args = ap.parse_args()
+    cfg = dict(CONFIGS[args.config if args.config != "c4" else "c4-f32"])
+    if args.k_off is not None:
+        cfg["k_off"] = args.k_off
+    if args.k_on is not None:
+        cfg["k_on"] = args.k_on
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        return run_reference(args, cfg, world, rank)
+
+    import torch
+    from paper_2309_08864_gb300 import inputs, so2dr
+    torch.cuda.set_device(local)
+    if args.kernel_case:
+        return run_kernel_case(args)
+    if args.link:
+        rows = {}
+        for ctas in (32, 64, 152):
+            rows[ctas] = so2dr.measure_link(1 << 30, sm_ctas=ctas, repeats=3)
+        print(json.dumps({"link_gbs": rows, "bytes": 1 << 30, "note": "keys by SM-copy CTA count; ce_* are "
+                          "cudaMemcpyAsync, sm_* a copy kernel over the mapped pinned buffer"}), flush=True)
+        return 0
+    if cfg.get("adjoint"):
+        return run_adjoint(args, cfg, world, rank, local)
+
+    if args.sweep:
+        hbm_peak, _ = measured_peaks()
+        return run_sweep(args, cfg, coeffs_of(cfg["coeffs"], inputs), make_input(cfg, inputs, so2dr, torch),
+                         hbm_peak, rank)
+    if args.config == "c4":
+        # the precision forms back to back on one box: FP32, BF16 and FP16
+        # storage (FP32 arithmetic), each with its error against the oracle
+        link = so2dr.measure_link(1 << 30, sm_ctas=64, repeats=3)
+        forms = {}
+        for dt in ("f32", "bf16", "f16"):
+            c = dict(CONFIGS["c4-" + dt])
+            forms[dt] = bench_config(args, c, "c4-" + dt, world, rank, local, torch, inputs, so2dr, link=link)
+        line = dict(forms["bf16"])
+        line["config"] = dict(line["config"], workload="3D 7-point star 1024^3, 128 steps, 1 GiB budget: FP32 vs "
+                                                       "BF16 vs FP16 storage (FP32 arithmetic); value: BF16")
+        line["precision_forms"] = {dt: {"value": f["value"], "unit": f["unit"], "ms_per_step": f["ms_per_step"],
+                                        "plan": {k: f["config"][k] for k in ("k_off", "k_on", "chunks", "rounds")},
+                                        "error_vs_oracle": f.get("error_vs_oracle"),
+                                        "path_roofline_frac": f["path_roofline"]["frac"]}
+                                   for dt, f in forms.items()}
+        line["precision_forms"]["bf16_over_f32"] = forms["bf16"]["value"] / forms["f32"]["value"]
+        line["precision_forms"]["f16_over_f32"] = forms["f16"]["value"] / forms["f32"]["value"]
+    else:
+        line = bench_config(args, cfg, args.config, world, rank, local, torch, inputs, so2dr)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

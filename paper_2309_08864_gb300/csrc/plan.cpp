@@ -164,6 +164,7 @@ bool build_forward_ooc_ex(const Plan& p, RunList& rl, size_t budget, const Forwa
     int nhost = opt.coef_array + 1;
     for (int v : opt.src_array) nhost = std::max(nhost, v + 1);
     for (int v : opt.dst_array) nhost = std::max(nhost, v + 1);
+    for (int v : opt.state_array) nhost = std::max(nhost, v + 1);
     // host arrays: the grid's source/destination per round, the face fields
     Emitter em(rl, nbuf + nhost, nbuf);
     const int64_t cin = rl.bufs[kBufIn].cap;
@@ -236,6 +237,21 @@ bool build_forward_ooc_ex(const Plan& p, RunList& rl, size_t budget, const Forwa
                 }
                 add_buf_access(em.tr, dst, out_lo, out_hi, 0, rl.bufs[dst].cap, true);
                 em.emit(op);
+                if (!last && t == 0 && j < opt.state_array.size()) {
+                    // an intermediate state of a single-step round: its owned
+                    // planes go to their own host array
+                    Op d = make_op(kOpD2H, kStreamD2H, t, i);
+                    d.host_array = opt.state_array[j];
+                    d.pub.src_buf = dst;
+                    d.pub.src_lo = d.pub.dst_lo = cg.s;
+                    d.pub.src_hi = d.pub.dst_hi = cg.e;
+                    d.pub.src_slot0 = cg.s - out_lo;
+                    d.pub.dst_buf = kHost;
+                    d.pub.dst_slot0 = cg.s;
+                    add_buf_access(em.tr, dst, cg.s, cg.e, cg.s - out_lo, rl.bufs[dst].cap, false);
+                    em.tr.access(em.host_res(d.host_array), cg.s, cg.e, true);
+                    em.emit(d);
+                }
                 src = dst;
                 in_lo = out_lo;
                 in_hi = out_hi;
@@ -556,11 +572,11 @@ double kernel_rate(const Plan& p, int depth) {
                 depth <= p.max_kon_auto;
     if (!fast) return p.dtype == SO2DR_F64 ? 20e9 : 100e9;
     if (p.r == 1) {
-        const double r1[5] = {0, 512e9, 750e9, 990e9, 990e9};
+        const double r1[5] = {0, 730e9, 1200e9, 1440e9, 1410e9};
         return r1[std::min(depth, 4)];
     }
-    if (p.r == 2) return depth >= 2 ? 450e9 : 380e9;
-    return p.r == 3 ? 320e9 : 280e9;
+    if (p.r == 2) return depth >= 2 ? 600e9 : 520e9;
+    return p.r == 3 ? 450e9 : 400e9;
 }
 
 double predict_ms(const Plan& p) {
@@ -571,12 +587,12 @@ double predict_ms(const Plan& p) {
     const double in_plane_bytes = (double)p.plane_bytes + (vc ? 6.0 * cells_plane * 4 : 0.0);
     const double host_h2d = (double)p.rounds * p.n0 * in_plane_bytes / (p.bw_h2d * 1e9);
     const double host_d2h = (double)p.rounds * p.interior_planes() * p.plane_bytes / (p.bw_d2h * 1e9);
-    // out-of-core launches run at about 80% of the in-core rate for chunks of
-    // 20-60 planes (measured: 0.77-0.82, the second compute stream filling
-    // part of each launch's last wave), and at nearly all of it for chunks of
-    // thousands of rows
+    // fused out-of-core launches run at 67-75% of the in-core rate for chunks
+    // of 35-45 planes (each launch fills and drains the pipeline of its fused
+    // levels), and at nearly all of it for chunks of thousands of rows;
+    // single-step launches keep the in-core rate
     const double pavg = (double)p.interior_planes() / std::max(1, p.d);
-    const double eff = std::max(0.8, pavg / (pavg + 12.0));
+    const double eff = p.k_on > 1 ? std::max(0.6, pavg / (pavg + 15.0)) : 1.0;
     const double kernel = comp * cells_plane / (eff * kernel_rate(p, p.k_on));
     const int L = (int)launch_depths(p.k_off, p.k_on).size();
     const double units = (double)std::max(1, p.d * p.rounds);
