@@ -19,7 +19,9 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <chrono>
+#include <cstdlib>
 #include <cstring>
 #include <vector>
 
@@ -44,9 +46,10 @@ struct PlaneRef {  // planes of a (possibly circular) arena buffer
 };
 
 struct AdjStepArgs {
-    PlaneRef lam, coef, u, grad;  // lambda_{t+1}, faces, u_t (radius-1 halo); gradient slab (owned)
-    void* lam_out;                // lambda_t on owned planes, slot z - s
-    int64_t s, e;                 // owned planes
+    PlaneRef lam, coef, u, grad;  // lambda_{t+1}, faces, u_t (radius-1 halo); gradient slab
+    void* lam_out;                // lambda_t on planes [s, e), slot z - s
+    int64_t s, e;                 // planes of lambda_t this launch computes
+    int64_t gs, ge;               // owned planes: the gradient accumulates here only
     int64_t n0, ny, nx;
     int first;                    // start the gradient from zero
 };
@@ -88,7 +91,8 @@ __global__ void __launch_bounds__(256) adjoint_step_kernel(const AdjStepArgs a) 
         }
         lo[(z - a.s) * plane + c] = acc;
         // dL/dc_f[q] += lambda_{t+1}[q] (u_t[q + e_f] - u_t[q]) on the owned cells
-        const int64_t gs = (z - a.s) * plane + c;
+        if (z < a.gs || z >= a.ge) continue;
+        const int64_t gs = (z - a.gs) * plane + c;
         const T uq = u[uz + c];
         for (int f = 0; f < 6; ++f) {
             T gv = a.first ? (T)0 : g[f * a.grad.field_stride + gs];
@@ -241,71 +245,85 @@ bool build_loss_list(const Plan& q, RunList& rl, size_t budget, int u_arr, int l
     return true;
 }
 
-// Buffers of the adjoint rounds.
-enum { kALam = 0, kACoef = 1, kAU = 2, kAG0 = 3, kAL0 = 5 };
+// Buffers of the adjoint rounds: circular region-shared inputs (lambda, the
+// face fields, the K states u_t), gradient and final-lambda slabs by chunk
+// parity, and two slabs for the intermediate lambdas of a round.
+enum { kALam = 0, kACoef = 1, kAG0 = 2, kAL0 = 4, kAX = 6, kAY = 7, kAU0 = 8 };
 
-int64_t adjoint_cin(const Plan& q) {
+// Capacity of the circular input buffers for rounds of K steps: a chunk's
+// inputs [s - K, e + K) and the next chunk's new planes, so that transfers
+// run one chunk ahead of the kernels.
+int64_t adjoint_cin(const Plan& q, int K) {
     int64_t cin = 0;
     for (int i = 0; i < q.d; ++i) {
-        ChunkGeom g = chunk_geom(q, i, 1);
-        int64_t next_hi = (i + 1 < q.d) ? chunk_geom(q, i + 1, 1).hi : q.n0 + chunk_geom(q, 0, 1).hi;
+        ChunkGeom g = chunk_geom(q, i, K);
+        int64_t next_hi = (i + 1 < q.d) ? chunk_geom(q, i + 1, K).hi : q.n0 + chunk_geom(q, 0, K).hi;
         cin = std::max(cin, std::max(g.b - g.a, next_hi - g.a));
     }
     return std::max<int64_t>(cin, 1);
 }
 
-size_t adjoint_layout(const Plan& q, std::vector<Buffer>* out) {
+size_t adjoint_layout(const Plan& q, int K, std::vector<Buffer>* out) {
     std::vector<Buffer> b;
     int64_t pmax = 0;
     for (int i = 0; i < q.d; ++i) pmax = std::max(pmax, q.starts[i + 1] - q.starts[i]);
-    int64_t cin = adjoint_cin(q), off = 0;
+    int64_t cin = adjoint_cin(q, K), off = 0;
     place(b, kALam, cin, q.plane_bytes, 1, off);
     place(b, kACoef, cin, 6 * q.plane_bytes, 6, off);
-    place(b, kAU, cin, q.plane_bytes, 1, off);
     for (int k = 0; k < 2; ++k) place(b, kAG0 + k, pmax, 6 * q.plane_bytes, 6, off);
     for (int k = 0; k < 2; ++k) place(b, kAL0 + k, pmax, q.plane_bytes, 1, off);
+    place(b, kAX, K >= 2 ? pmax + 2 * K : 0, q.plane_bytes, 1, off);
+    place(b, kAY, K >= 3 ? pmax + 2 * K : 0, q.plane_bytes, 1, off);
+    for (int k = 0; k < K; ++k) place(b, kAU0 + k, cin, q.plane_bytes, 1, off);
     off += kAlign;
     if (out) *out = b;
     return (size_t)off;
 }
 
-// Single-step adjoint rounds for times t_hi-1 down to t_lo.  state_arr(t) is
-// the host array holding u_t.  Rounds are numbered from round0 (virtual plane
-// base of the circular buffers).
+// Adjoint rounds for times t_hi-1 down to t_lo, K steps per round (the last
+// round of the span may be shorter).  A round reads lambda_{t+1} at its top
+// time, the face fields and its K states u_t, with a K-plane halo through the
+// circular buffers (each plane crosses the link once per round), runs K
+// single-step launches of the transposed stencil on the shrinking trapezoid,
+// accumulates dL/dc_f of all K steps on the chunk's owned planes in a device
+// slab, and sends lambda and the gradient back once.  state_arr(t) is the
+// host array holding u_t.
 template <typename F>
-void build_adjoint_list(const Plan& q, RunList& rl, int64_t t_lo, int64_t t_hi, int64_t T, int nhost, F state_arr) {
+void build_adjoint_list(const Plan& q, RunList& rl, int64_t t_lo, int64_t t_hi, int64_t T, int K, int nhost,
+                        F state_arr) {
     rl.ops.clear();
-    rl.arena_bytes = adjoint_layout(q, &rl.bufs);
+    rl.arena_bytes = adjoint_layout(q, K, &rl.bufs);
     const int nbuf = (int)rl.bufs.size();
     Emitter em(rl, nbuf + nhost, nbuf);
     const int64_t cin = rl.bufs[kALam].cap;
     int64_t g = 0;
     int rho = 0;
-    for (int64_t t = t_hi - 1; t >= t_lo; --t, ++rho) {
+    for (int64_t top = t_hi; top > t_lo; top -= K, ++rho) {
+        const int kk = (int)std::min<int64_t>(K, top - t_lo);
         const int64_t V = (int64_t)rho * q.n0;
         for (int i = 0; i < q.d; ++i, ++g) {
-            ChunkGeom cg = chunk_geom(q, i, 1);
+            ChunkGeom cg = chunk_geom(q, i, kk);
             const int k = (int)(g % 2);
-            // region-shared inputs: lambda_{t+1}, the face fields, u_t
+            // region-shared inputs: lambda_{top}, the face fields, u_{top-1} .. u_{top-kk}
             if (cg.hi > cg.lo) {
-                const int bufs[3] = {kALam, kACoef, kAU};
-                const int arrs[3] = {kHLam, kHCoef, state_arr(t)};
-                for (int f = 0; f < 3; ++f) {
+                for (int f = 0; f < 2 + kk; ++f) {
+                    const int buf = f == 0 ? kALam : f == 1 ? kACoef : kAU0 + (f - 2);
+                    const int arr = f == 0 ? kHLam : f == 1 ? kHCoef : state_arr(top - 1 - (f - 2));
                     Op op = make_op(kOpH2D, kStreamH2D, rho, i);
-                    op.host_array = arrs[f];
+                    op.host_array = arr;
                     op.nfields = f == 1 ? 6 : 1;
                     op.pub.src_lo = op.pub.dst_lo = cg.lo;
                     op.pub.src_hi = op.pub.dst_hi = cg.hi;
                     op.pub.src_slot0 = cg.lo;
-                    op.pub.dst_buf = bufs[f];
+                    op.pub.dst_buf = buf;
                     op.pub.dst_slot0 = floor_mod(V + cg.lo, cin);
-                    em.tr.access(em.host_res(arrs[f]), cg.lo, cg.hi, false);
-                    add_buf_access(em.tr, bufs[f], cg.lo, cg.hi, op.pub.dst_slot0, cin, true);
+                    em.tr.access(em.host_res(arr), cg.lo, cg.hi, false);
+                    add_buf_access(em.tr, buf, cg.lo, cg.hi, op.pub.dst_slot0, cin, true);
                     em.emit(op);
                 }
             }
             // the gradient accumulated so far on the owned planes
-            if (t != T - 1) {
+            if (top != T) {
                 Op op = make_op(kOpH2D, kStreamH2D, rho, i);
                 op.host_array = kHGrad;
                 op.nfields = 6;
@@ -318,33 +336,50 @@ void build_adjoint_list(const Plan& q, RunList& rl, int64_t t_lo, int64_t t_hi, 
                 em.tr.access(kAG0 + k, 0, cg.e - cg.s, true);
                 em.emit(op);
             }
-            Op op = make_op(kOpKernel, (g % 2) ? kStreamCompute2 : kStreamCompute, rho, i);
-            op.fn = kFnAdjoint;
-            op.pub.depth = 1;
-            op.pub.src_buf = kALam;
-            op.pub.src_lo = cg.a;
-            op.pub.src_hi = cg.b;
-            op.pub.src_slot0 = floor_mod(V + cg.a, cin);
-            op.aux_buf = kACoef;
-            op.aux_lo = cg.a;
-            op.aux_slot0 = op.pub.src_slot0;
-            op.aux2_buf = kAU;
-            op.aux2_lo = cg.a;
-            op.aux2_slot0 = op.pub.src_slot0;
-            op.aux3_buf = kAG0 + k;
-            op.aux3_lo = cg.s;
-            op.aux3_slot0 = 0;
-            op.pub.dst_buf = kAL0 + k;
-            op.pub.dst_lo = cg.s;
-            op.pub.dst_hi = cg.e;
-            op.arg1 = (t == T - 1);
-            for (int b : {kALam, kACoef, kAU})
-                add_buf_access(em.tr, b, cg.a, cg.b, op.pub.src_slot0, cin, false);
-            em.tr.access(kAG0 + k, 0, cg.e - cg.s, true);
-            em.tr.access(kAL0 + k, 0, cg.e - cg.s, true);
-            em.emit(op);
-            // lambda_t and the gradient back to the host (every owned plane:
-            // the adjoint also changes the boundary cells of lambda)
+            // kk launches: lambda_{top-1-m} on [s - (kk-1-m), e + (kk-1-m))
+            int src = kALam;
+            int64_t in_lo = cg.a, in_hi = cg.b, src_slot0 = floor_mod(V + cg.a, cin), scap = cin;
+            const int stream = (g % 2) ? kStreamCompute2 : kStreamCompute;
+            for (int m = 0; m < kk; ++m) {
+                const bool last = m + 1 == kk;
+                const int64_t h = kk - 1 - m;
+                const int64_t lo = std::max<int64_t>(0, cg.s - h), hi = std::min<int64_t>(q.n0, cg.e + h);
+                const int dst = last ? kAL0 + k : ((m % 2 == 0) ? kAX : kAY);
+                Op op = make_op(kOpKernel, stream, rho, i);
+                op.fn = kFnAdjoint;
+                op.pub.depth = 1;
+                op.pub.src_buf = src;
+                op.pub.src_lo = in_lo;
+                op.pub.src_hi = in_hi;
+                op.pub.src_slot0 = src_slot0;
+                op.aux_buf = kACoef;
+                op.aux_lo = cg.a;
+                op.aux_slot0 = floor_mod(V + cg.a, cin);
+                op.aux2_buf = kAU0 + m;
+                op.aux2_lo = cg.a;
+                op.aux2_slot0 = floor_mod(V + cg.a, cin);
+                op.aux3_buf = kAG0 + k;
+                op.aux3_lo = cg.s;
+                op.aux3_slot0 = 0;
+                op.arg2 = cg.e;
+                op.pub.dst_buf = dst;
+                op.pub.dst_lo = lo;
+                op.pub.dst_hi = hi;
+                op.arg1 = (top == T && m == 0);
+                add_buf_access(em.tr, src, in_lo, in_hi, src_slot0, scap, false);
+                add_buf_access(em.tr, kACoef, cg.a, cg.b, op.aux_slot0, cin, false);
+                add_buf_access(em.tr, kAU0 + m, cg.a, cg.b, op.aux2_slot0, cin, false);
+                em.tr.access(kAG0 + k, 0, cg.e - cg.s, true);
+                em.tr.access(dst, 0, hi - lo, true);
+                em.emit(op);
+                src = dst;
+                in_lo = lo;
+                in_hi = hi;
+                src_slot0 = 0;
+                scap = rl.bufs[dst].cap;
+            }
+            // lambda_{top-kk} and the gradient back to the host (every owned
+            // plane: the adjoint also changes the boundary cells of lambda)
             for (int f = 0; f < 2; ++f) {
                 Op d = make_op(kOpD2H, kStreamD2H, rho, i);
                 d.host_array = f ? kHGrad : kHLam;
@@ -386,7 +421,7 @@ int fit_d(Plan& q, int dmin, size_t limit, F arena) {
 
 }  // namespace
 
-size_t adjoint_arena_bytes(const Plan& q) { return adjoint_layout(q, nullptr); }
+size_t adjoint_arena_bytes(const Plan& q) { return adjoint_layout(q, 1, nullptr); }
 
 size_t adjoint_workspace_bytes(const Plan& p) {
     if (p.kind != SO2DR_VARCOEF_STAR) return (size_t)(p.n0 * p.plane_bytes);
@@ -424,6 +459,8 @@ int enqueue_aux_kernel(so2dr_plan_s* P, const RunList& rl, const Op& op, cudaStr
         a.lam_out = buf(o.dst_buf);
         a.s = o.dst_lo;
         a.e = o.dst_hi;
+        a.gs = op.aux3_lo;
+        a.ge = op.arg2;
         a.n0 = p.n0;
         a.ny = p.ny;
         a.nx = p.nx;
@@ -646,19 +683,70 @@ int so2dr_adjoint(so2dr_plan_t P, const void* host_u0, const void* host_coeff_fi
         std::memset(host_grad_coeffs, 0, (size_t)(6 * p.n0 * p.plane_cells * cb));
         return SO2DR_OK;
     }
-    // 3. segments, last first: recompute states, then adjoint rounds
+    // 3. segments, last first: recompute states, then adjoint rounds.  The
+    // rounds take K steps (K <= C) where the budget admits it: per round the
+    // face fields and lambda cross the link once and the gradient once each
+    // way, so K steps per round divide that traffic by K; the cost below
+    // weighs those bytes against the per-chunk copy and launch overhead of the
+    // smaller chunks a larger K forces.
+    int K = 0;
     Plan qa = p;
-    if (!fit_d(qa, 1, limit, [](const Plan& x) { return adjoint_layout(x, nullptr); }))
-        return set_error(SO2DR_E_INFEASIBLE, "adjoint rounds do not fit the bound arena");
+    {
+        // SO2DR_ADJOINT_STEPS pins K (or the largest K below it that fits)
+        const char* ek = std::getenv("SO2DR_ADJOINT_STEPS");
+        const int kpin = ek ? (int)std::min<int64_t>(std::max(1, std::atoi(ek)), C) : 0;
+        double best = 0;
+        for (int k = 1; k <= (int)std::min<int64_t>(C, 16); ++k) {
+            if (kpin > 0 && k > kpin) continue;
+            Plan q = p;
+            if (!fit_d(q, 1, limit, [k](const Plan& x) { return adjoint_layout(x, k, nullptr); })) continue;
+            const double grid_b = (double)p.n0 * p.plane_bytes;
+            const double link_s = grid_b * (14.0 + k) / 170e9;           // inputs of one round
+            const double ops_s = (double)q.d * (24.0 + 2.0 * k) * 4e-6;  // copies and launches
+            const double cost = kpin > 0 ? -k : (link_s + ops_s) * std::ceil((double)C / k);
+            if (K == 0 || cost < best) {
+                K = k;
+                best = cost;
+                qa = q;
+            }
+        }
+    }
+    if (!K) return set_error(SO2DR_E_INFEASIBLE, "adjoint rounds do not fit the bound arena");
     for (int64_t j = S - 1; j >= 0; --j) {
         const int64_t ts = j * C, len = std::min(C, T - ts);
-        // u_{ts+m}, m = 1..len-1, into the segment states (single-step rounds)
-        for (int64_t m = 1; m < len; ++m) {
-            rc = forward_pipeline(P, 1, 1, m == 1 ? ckpt_arr(j) : seg_arr(m - 1), seg_arr(m), h, limit, stats);
-            if (rc) return rc;
+        // u_{ts+m}, m = 1..len-1, into the segment states: one round of
+        // single-step launches that sends every intermediate state back, or,
+        // where that round does not fit, one round per step
+        if (len >= 2) {
+            ForwardOpts o;
+            o.all_planes = true;
+            o.coef_array = kHCoef;
+            o.src_array.push_back(ckpt_arr(j));
+            o.dst_array.push_back(seg_arr(len - 1));
+            for (int64_t m = 1; m + 1 < len; ++m) o.state_array.push_back(seg_arr(m));
+            Plan q = p;
+            q.T = len - 1;
+            q.k_off = (int)(len - 1);
+            q.k_on = 1;
+            q.rounds = 1;
+            RunList rl;
+            if (fit_d(q, 1, limit, [](const Plan& x) { return forward_arena_bytes(x); }) &&
+                build_forward_ooc_ex(q, rl, limit, o)) {
+                Plan saved = P->p;
+                P->p = q;
+                rc = run_list(P, rl, h, stats);
+                P->p = saved;
+                if (rc) return rc;
+            } else {
+                for (int64_t m = 1; m < len; ++m) {
+                    rc = forward_pipeline(P, 1, 1, m == 1 ? ckpt_arr(j) : seg_arr(m - 1), seg_arr(m), h, limit,
+                                          stats);
+                    if (rc) return rc;
+                }
+            }
         }
         RunList rl;
-        build_adjoint_list(qa, rl, ts, ts + len, T, (int)h.base.size(),
+        build_adjoint_list(qa, rl, ts, ts + len, T, K, (int)h.base.size(),
                            [&](int64_t t) { return t == ts ? ckpt_arr(j) : seg_arr(t - ts); });
         if (rl.arena_bytes > limit) return set_error(SO2DR_E_INFEASIBLE, "adjoint rounds do not fit");
         Plan saved = P->p;

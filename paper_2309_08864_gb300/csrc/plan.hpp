@@ -48,7 +48,7 @@ struct Op {
     int64_t aux2_lo = 0, aux2_slot0 = 0;
     int aux3_buf = -1;
     int64_t aux3_lo = 0, aux3_slot0 = 0;
-    int64_t arg0 = 0, arg1 = 0;  // kernel-specific integers
+    int64_t arg0 = 0, arg1 = 0, arg2 = 0;  // kernel-specific integers
     bool waited = false;    // some later op waits on this op's completion event
 };
 
@@ -160,6 +160,9 @@ struct ForwardOpts {
     std::vector<int> dst_array;  // host array each round writes (default: 0)
     bool all_planes = false;     // write back the axis-0 boundary planes too
     int coef_array = 1;          // host array of the face fields
+    // round 0 only, single-step launches: host array receiving the state after
+    // launch j (j = 0 .. k'-2; the last state goes to dst_array[0])
+    std::vector<int> state_array;
 };
 
 // Forward op list with per-round source/destination host arrays.

@@ -21,14 +21,21 @@ def _problem(dims, dtype, seed_u=1, seed_t=2):
     return u0, faces, tgt, pin(u0), pin(faces), pin(tgt)
 
 
-@pytest.mark.parametrize("dtype,dims,T,C,budget", [
-    (so2dr.F64, (20, 18, 24), 11, 4, 384 << 10),   # 9 chunks, segments 4, 4, 3
-    (so2dr.F32, (24, 20, 28), 11, 4, 256 << 10),   # 11 chunks
-    (so2dr.F32, (30, 17, 20), 8, 8, 0),            # one segment, 3 chunks
-    (so2dr.F32, (16, 12, 16), 5, 1, 64 << 10),     # a checkpoint every step, 5 forward chunks
+@pytest.mark.parametrize("dtype,dims,T,C,budget,K", [
+    (so2dr.F64, (20, 18, 24), 11, 4, 384 << 10, 0),   # 9 chunks, segments 4, 4, 3
+    (so2dr.F64, (20, 18, 24), 11, 4, 384 << 10, 3),   # rounds of 3 steps: 3 + 1 per segment of 4
+    (so2dr.F32, (24, 20, 28), 11, 4, 256 << 10, 0),   # 11 chunks
+    (so2dr.F32, (24, 20, 28), 11, 4, 256 << 10, 2),   # rounds of 2 steps
+    (so2dr.F32, (30, 17, 20), 8, 8, 0, 0),            # one segment, 3 chunks
+    (so2dr.F32, (30, 17, 20), 8, 8, 0, 8),            # one segment in one adjoint round
+    (so2dr.F32, (16, 12, 16), 5, 1, 64 << 10, 0),     # a checkpoint every step, 5 forward chunks
 ])
-def test_adjoint_matches_oracle(dtype, dims, T, C, budget):
+def test_adjoint_matches_oracle(dtype, dims, T, C, budget, K, monkeypatch):
+    """K > 0 pins the steps per adjoint round (SO2DR_ADJOINT_STEPS): the
+    gradient is accumulated over K steps on the device before it goes back."""
     import torch
+    if K:
+        monkeypatch.setenv("SO2DR_ADJOINT_STEPS", str(K))
     u0, faces, tgt, tu0, tf, tt = _problem(dims, dtype)
     plan = so2dr.Plan(dims, 1, "varcoef", None, T, min_chunks=3, k_on=2, k_off=C, budget_bytes=budget,
                       dtype=dtype)
