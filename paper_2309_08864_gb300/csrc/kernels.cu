@@ -21,8 +21,7 @@ int tile_edge(int H) {
 }  // namespace
 
 bool fast_star3d_supported(int r, int depth) {
-    return (r == 1 && depth >= 1 && depth <= 4) || (r == 2 && depth >= 1 && depth <= 2) ||
-           ((r == 3 || r == 4) && depth == 1);
+    return (r == 1 && depth >= 1 && depth <= 4) || (r >= 2 && r <= 4 && depth >= 1 && depth <= 2);
 }
 
 bool fast_star3d_row_ok(int64_t nx, int esize) { return nx % (esize == 4 ? 4 : 8) == 0; }
@@ -98,7 +97,9 @@ LaunchShape stencil_launch_shape(int shape, int r, int depth, int64_t ny, int64_
             case 33: fast_shape<2, 1>(ls, ny, nx, esize); break;
             case 34: fast_shape<2, 2>(ls, ny, nx, esize); break;
             case 49: fast_shape<3, 1>(ls, ny, nx, esize); break;
+            case 50: fast_shape<3, 2>(ls, ny, nx, esize); break;
             case 65: fast_shape<4, 1>(ls, ny, nx, esize); break;
+            case 66: fast_shape<4, 2>(ls, ny, nx, esize); break;
         }
         if (ls.ok) return ls;
     }

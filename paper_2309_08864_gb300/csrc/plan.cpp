@@ -571,12 +571,15 @@ double kernel_rate(const Plan& p, int depth) {
     bool fast = p.kind == SO2DR_STAR && p.ndim == 3 && p.dtype != SO2DR_F64 && p.nx % 4 == 0 &&
                 depth <= p.max_kon_auto;
     if (!fast) return p.dtype == SO2DR_F64 ? 20e9 : 100e9;
+    // (in-core, 1024^3 FP32; radius 3 and 4 at depth 2 run 2 rows per warp
+    // and 2R = 6 or 8 unrolled phases, far slower than one level)
     if (p.r == 1) {
-        const double r1[5] = {0, 730e9, 1200e9, 1440e9, 1410e9};
+        const double r1[5] = {0, 740e9, 1220e9, 1450e9, 1400e9};
         return r1[std::min(depth, 4)];
     }
-    if (p.r == 2) return depth >= 2 ? 600e9 : 520e9;
-    return p.r == 3 ? 450e9 : 400e9;
+    if (p.r == 2) return depth >= 2 ? 830e9 : 710e9;
+    if (p.r == 3) return depth >= 2 ? 330e9 : 565e9;
+    return depth >= 2 ? 110e9 : 480e9;
 }
 
 double predict_ms(const Plan& p) {
@@ -756,17 +759,24 @@ int build_plan(Plan& p, int ndim, const int64_t* dims, int radius, int kind, con
                 }
             }
         }
-        // Among the candidates predicted within 2% of the best, take the one
-        // with the fewest rounds (least host-link traffic), then the lowest
+        // Among the candidates predicted within 2% of the best, take the ones
+        // with the fewest rounds (least host-link traffic); among those
+        // predicted within 1% of their lowest, the smallest k_off (least
+        // redundant work, when the link bounds them alike), then the lowest
         // prediction: the model cannot tell them apart, and the host link,
         // shared with the rest of the host, is the most variable resource.
         int brounds = std::numeric_limits<int>::max();
+        for (const Candidate& c : feasible)
+            if (c.predicted_ms <= 1.02 * best) brounds = std::min(brounds, (int)((T + c.k_off - 1) / c.k_off));
+        double bmin = std::numeric_limits<double>::infinity();
+        for (const Candidate& c : feasible)
+            if (c.predicted_ms <= 1.02 * best && (int)((T + c.k_off - 1) / c.k_off) == brounds)
+                bmin = std::min(bmin, c.predicted_ms);
         double bms = std::numeric_limits<double>::infinity();
         for (const Candidate& c : feasible) {
-            if (c.predicted_ms > 1.02 * best) continue;
-            const int rounds = (int)((T + c.k_off - 1) / c.k_off);
-            if (rounds < brounds || (rounds == brounds && c.predicted_ms < bms)) {
-                brounds = rounds;
+            if (c.predicted_ms > 1.02 * best || (int)((T + c.k_off - 1) / c.k_off) != brounds) continue;
+            if (c.predicted_ms > 1.01 * bmin) continue;
+            if (!bd || c.k_off < bko || (c.k_off == bko && c.predicted_ms < bms)) {
                 bms = c.predicted_ms;
                 bko = c.k_off;
                 bkn = c.k_on;

@@ -30,8 +30,11 @@
 //    boundary cells are the ring's columns select those cells by a per-lane
 //    predicate; warps with boundary rows, and phases with a fixed plane in
 //    flight, select per cell on a slower path;
-//  * phases in which every level is active and no fixed plane is in flight
-//    run a straight-line body without per-level tests.
+//  * a phase runs one body per boundary mode (no boundary cell, ring columns,
+//    per-cell masks); for radius 1 the phases in which every level is active
+//    run straight-line bodies without per-level tests, for larger radii (2R
+//    phases of longer bodies) a uniform per-level test keeps the code inside
+//    the instruction cache.
 // The valid area shrinks by R per level in y and x: the compute-area
 // adjustment of Algorithm 1 applied inside a launch.
 //
@@ -48,9 +51,11 @@ namespace so2dr {
 
 // Tile shape per (R, K).  Fused depths: 8 warps of 4 rows, whose partial sums
 // (K * 2R * 16 per thread) and carried cells fit the 255-register limit of a
-// 256-thread CTA.  One level: 8 warps of 2 rows, two CTAs per SM.
+// 256-thread CTA; radius 3 and 4 fuse two levels with 2 rows per warp (the
+// 2R = 8 partial sums per cell and level leave no room for more).  One level:
+// 8 warps of 2 rows, two CTAs per SM.
 template <int R, int K> struct StarShape {
-    static constexpr int VY = K == 1 ? 2 : 4;
+    static constexpr int VY = (K == 1 || R >= 3) ? 2 : 4;
     static constexpr int NW = 8;
     static constexpr int NT = NW * 32;
     static constexpr bool CARRY = K > 1;                // own cells of a level stay in registers
@@ -302,24 +307,19 @@ struct StarTB {
         }
     }
 
-    // every level active, no fixed plane in flight; levels run from the
-    // deepest down, so that level L reads the carried cells of level L-1
-    // before level L-1 replaces them
-    template <int L, int PH, int MODE>
-    __device__ __forceinline__ void levels_steady(int p) {
-        level_body<L, PH, MODE>(p);
-        if constexpr (L > 0) levels_steady<L - 1, PH, MODE>(p);
-    }
-
-    // head and tail of the stream, and the fixed planes
-    template <int L, int PH>
-    __device__ __forceinline__ void levels_checked(int p) {
-        const int zp = za + p - L * (R + 1);
-        if (zp >= lev_lo(L) && zp < lev_hi(L)) {
-            if (wmode == kBndNone && zp >= 2 * R && zp < n0 - R) level_body<L, PH, kBndNone>(p);
-            else level_body<L, PH, kBndCells>(p);
+    // the levels of one phase, from the deepest down, so that level L reads
+    // the carried cells of level L-1 before level L-1 replaces them; in the
+    // head and tail of the stream a level runs only while its arrivals can
+    // reach the requested output (ALL: a phase known to need every level)
+    template <int L, int PH, int MODE, bool ALL>
+    __device__ __forceinline__ void levels(int p, bool all) {
+        if constexpr (ALL) {
+            level_body<L, PH, MODE>(p);
+        } else {
+            const int zp = za + p - L * (R + 1);
+            if (all || (zp >= lev_lo(L) && zp < lev_hi(L))) level_body<L, PH, MODE>(p);
         }
-        if constexpr (L > 0) levels_checked<L - 1, PH>(p);
+        if constexpr (L > 0) levels<L - 1, PH, MODE, ALL>(p, all);
     }
 
     // phase p = p0 + PH; false when an input copy did not land in time
@@ -339,10 +339,22 @@ struct StarTB {
         }
         // the arrivals of this phase span planes za + p - (K-1)(R+1) .. za + p;
         // a fixed plane among their targets (z' - R .. z') needs the cell path
-        const bool steady = p >= ps_lo && p < ps_hi && za + p - (K - 1) * (R + 1) >= 2 * R && za + p < n0 - R;
-        if (steady && wmode == kBndNone) levels_steady<K - 1, PH, kBndNone>(p);
-        else if (steady && wmode == kBndColumns) levels_steady<K - 1, PH, kBndColumns>(p);
-        else levels_checked<K - 1, PH>(p);
+        const bool all = p >= ps_lo && p < ps_hi;
+        const bool fixed = za + p - (K - 1) * (R + 1) < 2 * R || za + p >= n0 - R;
+        if constexpr (R == 1) {
+            // short bodies: straight-line phases for the steady state, and
+            // the checked ones for head, tail and fixed planes
+            if (all && !fixed && wmode == kBndNone) levels<K - 1, PH, kBndNone, true>(p, true);
+            else if (all && !fixed && wmode == kBndColumns) levels<K - 1, PH, kBndColumns, true>(p, true);
+            else if (fixed || wmode != kBndNone) levels<K - 1, PH, kBndCells, false>(p, all);
+            else levels<K - 1, PH, kBndNone, false>(p, all);
+        } else {
+            // long bodies (2R phases of them): one body per boundary mode,
+            // which keeps the loop inside the instruction cache
+            if (fixed || wmode == kBndCells) levels<K - 1, PH, kBndCells, false>(p, all);
+            else if (wmode == kBndColumns) levels<K - 1, PH, kBndColumns, false>(p, all);
+            else levels<K - 1, PH, kBndNone, false>(p, all);
+        }
         if constexpr (PH + 1 < W2) return phase<PH + 1>(p0);
         return true;
     }

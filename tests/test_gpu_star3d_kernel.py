@@ -16,7 +16,7 @@ from tests.test_gpu_parity import TOL, _coeffs, check_case
 
 pytestmark = pytest.mark.gpu
 
-CASES = [(1, 1), (1, 2), (1, 3), (1, 4), (2, 1), (2, 2), (3, 1), (4, 1)]
+CASES = [(1, 1), (1, 2), (1, 3), (1, 4), (2, 1), (2, 2), (3, 1), (3, 2), (4, 1), (4, 2)]
 
 
 @pytest.mark.parametrize("dtype", [so2dr.F32, so2dr.BF16, so2dr.F16])

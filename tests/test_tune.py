@@ -35,11 +35,15 @@ def test_candidates_are_ranked_and_the_automatic_plan_follows_the_band_rule(prob
         assert e["status"] == 0 and e["measured_ms"] == -1.0
         assert 1 <= e["k_on"] <= e["k_off"] and e["chunks"] >= 1
     # the automatic plan: among candidates predicted within 2% of the best,
-    # the one with the fewest rounds (least host-link traffic), then the lowest prediction
+    # those with the fewest rounds (least host-link traffic); among these,
+    # within 1% of their lowest prediction, the smallest k_off, then the
+    # lowest prediction
     auto = so2dr.Plan(**prob, link_gbs=(200.0, 190.0), hbm_gbs=6800.0)
     rounds = lambda e: -(-prob["time_steps"] // e["k_off"])
     band = [e for e in t if e["predicted_ms"] <= 1.02 * preds[0]]
-    pick = min(band, key=lambda e: (rounds(e), e["predicted_ms"]))
+    fewest = [e for e in band if rounds(e) == min(rounds(x) for x in band)]
+    low = min(e["predicted_ms"] for e in fewest)
+    pick = min([e for e in fewest if e["predicted_ms"] <= 1.01 * low], key=lambda e: (e["k_off"], e["predicted_ms"]))
     assert _plan_key(auto) == tuple(pick[k] for k in KEYS)
 
 
