@@ -471,6 +471,9 @@ def run_adjoint(args, cfg, world, rank, local):
     value = world * cells * args.steps / (ms * 1e-3) / 1e9
     h2d = stats[-1]["h2d_bytes"]
     d2h = stats[-1]["d2h_bytes"]
+    if mode == 3:
+        # zero-copy input: the first launches read the new planes over the link
+        h2d = info["h2d_bytes_per_run"]
     line = {"metric": "Gcell-updates/s out-of-core on 1 GB300 (forward + adjoint updates)", "value": value,
             "unit": "Gcell/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -559,7 +562,7 @@ def bench_config(args, cfg, name, world, rank, local, torch, inputs, so2dr, link
     else:
         plan = make_plan(cfg, coeffs, so2dr)
     info = plan.info
-    mode = {"so2dr": 0, "incore": 1, "resreu": 2}[args.mode]
+    mode = {"so2dr": 0, "incore": 1, "resreu": 2, "zerocopy": 3}[args.mode]
     plan.bind(in_core=mode)
     for _ in range(args.warmup):
         plan.run(host, in_core=mode)
@@ -625,6 +628,9 @@ def bench_config(args, cfg, name, world, rank, local, torch, inputs, so2dr, link
     t_pool = max(2.0 * Nb * info["rounds"] / (LINK_BIDIR_GBS * 1e9), pr["t_hbm_s"])
     h2d = stats[-1]["h2d_bytes"]
     d2h = stats[-1]["d2h_bytes"]
+    if mode == 3:
+        # zero-copy input: the first launches read the new planes over the link
+        h2d = info["h2d_bytes_per_run"]
     line = {
         "metric": "Gcell-updates/s out-of-core on 1 GB300; % of max(host-link, HBM) roofline",
         "value": value, "unit": "Gcell/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -647,8 +653,10 @@ def bench_config(args, cfg, name, world, rank, local, torch, inputs, so2dr, link
                           "frac_min_rounds": prm["t_roof_s"] / t_meas, "min_rounds": rmin, "k_off_max": kmax,
                           "frac_vs_pool_link": t_pool / t_meas, "link_pool_bidir_gbs": LINK_BIDIR_GBS,
                           "host_bytes": 2.0 * Nb * info["rounds"], "hbm_bytes": pr["hbm_bytes"], "hbm_gbs": hbm_peak,
-                          "stream_gbs_during_run": {"h2d": h2d / (stats[-1]["h2d_ms"] * 1e-3) / 1e9,
-                                                    "d2h": d2h / (stats[-1]["d2h_ms"] * 1e-3) / 1e9}},
+                          "stream_gbs_during_run": {"h2d": (stats[-1]["h2d_bytes"] / (stats[-1]["h2d_ms"] * 1e-3) / 1e9
+                                                            if stats[-1]["h2d_ms"] > 0 else None),
+                                                    "d2h": (d2h / (stats[-1]["d2h_ms"] * 1e-3) / 1e9
+                                                            if stats[-1]["d2h_ms"] > 0 else None)}},
         "roofline": {"bound": "alu" if alu_bound else "hbm",
                      "achieved": achieved_tf if alu_bound else achieved,
                      "peak": ALU_PEAK_TFLOPS if alu_bound else hbm_peak,
@@ -696,11 +704,12 @@ def main():
     ap.add_argument("--kind", default="star", choices=["star", "box"], help="--kernel-case stencil (box: 2D n x n)")
     ap.add_argument("--launches", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", default="so2dr", choices=["so2dr", "incore", "resreu"],
+    ap.add_argument("--mode", default="so2dr", choices=["so2dr", "incore", "resreu", "zerocopy"],
                     help="so2dr: the out-of-core SO2DR pipeline (default); incore: the whole grid on the "
                          "device, same launch depths, transfers outside the timed region; resreu: the "
                          "redundancy-free out-of-core comparison code (single-step launches, region "
-                         "sharing of intermediate results)")
+                         "sharing of intermediate results); zerocopy: the SO2DR pipeline whose first "
+                         "launches read the new planes from the mapped host grid (no host-to-device copy)")
     ap.add_argument("--tune", type=int, default=0,
                     help="measured autotune before timing: time the model's N best plans (so2dr_autotune) "
                          "and benchmark the fastest")

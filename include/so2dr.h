@@ -112,6 +112,7 @@ typedef struct {
                                 the next chunk's last launch)                        */
     size_t arena_bytes_result_reuse; /* arena of mode 2 of so2dr_run (0: unavailable) */
     int result_reuse_chunks; /* chunks mode 2 uses                                  */
+    int zero_copy;           /* 1: mode 3 of so2dr_run (zero-copy input) is available */
 } so2dr_plan_info_t;
 
 /* Filled by so2dr_run / so2dr_adjoint when the caller passes a non-NULL pointer. */
@@ -299,6 +300,16 @@ int so2dr_bind(so2dr_plan_t plan, void* device_arena, size_t arena_bytes,
  *                  chunking (plan_info().result_reuse_chunks) and arena
  *                  (plan_info().arena_bytes_result_reuse); constant
  *                  coefficients only.
+ *                  3: mode 0 with zero-copy input: no host-to-device copy
+ *                  of the grid; the first launch of each chunk reads the
+ *                  chunk's new planes from the pinned host grid through its
+ *                  device mapping (cudaHostGetDevicePointer) and writes them
+ *                  into the circular buffer, where the next chunk finds its
+ *                  shared region (a GB300 option over NVLink-C2C, not in the
+ *                  paper).  Same arena and result as mode 0; 3D constant-
+ *                  coefficient stars with FP32/BF16/FP16 storage whose every
+ *                  first launch runs the register-streaming kernel
+ *                  (plan_info().zero_copy).
  *   stats          optional timings.
  */
 int so2dr_run(so2dr_plan_t plan, void* host_grid, const void* host_coeff_fields, int in_core,
@@ -429,7 +440,7 @@ void so2dr_destroy(so2dr_plan_t plan);
 const char* so2dr_strerror(int status);
 const char* so2dr_last_error(void);
 
-/* ABI version of this header (bumped on any incompatible change): 3. */
+/* ABI version of this header (bumped on any incompatible change): 5. */
 int so2dr_abi_version(void);
 
 #ifdef __cplusplus

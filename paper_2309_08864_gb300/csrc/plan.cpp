@@ -8,6 +8,9 @@
 
 namespace so2dr {
 
+bool fast_star3d_supported(int r, int depth);
+bool fast_star3d_row_ok(int64_t nx, int esize);
+
 
 int64_t elem_size(int dtype) {
     switch (dtype) {
@@ -177,7 +180,7 @@ bool build_forward_ooc_ex(const Plan& p, RunList& rl, size_t budget, const Forwa
             ChunkGeom cg = chunk_geom(p, i, kk);
             // (Algorithm 1) transfer the chunk's new planes to the GPU
             if (cg.hi > cg.lo) {
-                for (int f = 0; f < (vc ? 2 : 1); ++f) {
+                for (int f = opt.zero_copy ? 1 : 0; f < (vc ? 2 : 1); ++f) {
                     int buf = f ? kBufCoef : kBufIn;
                     Op op = make_op(kOpH2D, kStreamH2D, t, i);
                     op.host_array = f ? opt.coef_array : src_of(t);
@@ -229,6 +232,15 @@ bool build_forward_ooc_ex(const Plan& p, RunList& rl, size_t budget, const Forwa
                 op.pub.dst_slot0 = 0;
                 int64_t scap = rl.bufs[src].cap;
                 add_buf_access(em.tr, src, in_lo, in_hi, src_slot0, scap, false);
+                if (opt.zero_copy && j == 0 && cg.hi > cg.lo) {
+                    // the new planes come from the host grid and go into the
+                    // circular buffer (for the next chunk's shared region)
+                    op.host_src = src_of(t);
+                    op.host_lo = cg.lo;
+                    op.host_hi = cg.hi;
+                    em.tr.access(em.host_res(src_of(t)), cg.lo, cg.hi, false);
+                    add_buf_access(em.tr, kBufIn, cg.lo, cg.hi, floor_mod(V + cg.lo, cin), cin, true);
+                }
                 if (vc) {
                     op.aux_buf = kBufCoef;
                     op.aux_lo = cg.a;
@@ -807,6 +819,20 @@ int build_plan(Plan& p, int ndim, const int64_t* dims, int radius, int kind, con
     build_forward_in_core(p, p.ic);
     if (p.kind != SO2DR_VARCOEF_STAR && p.rounds > 0)
         if (!build_result_reuse(p, p.rr, p.budget, &p.rr_chunks)) p.rr_chunks = 0;
+    // zero-copy input: the first launch of every chunk must run the 3D star
+    // kernel (the one that can read mapped host planes)
+    p.zc_ok = false;
+    if (p.kind == SO2DR_STAR && p.ndim == 3 && p.dtype != SO2DR_F64 && p.rounds > 0 &&
+        fast_star3d_row_ok(p.nx, (int)p.elem_bytes) && !std::getenv("SO2DR_GENERIC_KERNEL")) {
+        bool all_fast = true;
+        for (int t = 0; t < p.rounds; ++t) {
+            const int kk = round_steps(p.T, p.k_off, t);
+            all_fast = all_fast && fast_star3d_supported(p.r, std::min(kk, p.k_on));
+        }
+        ForwardOpts zo;
+        zo.zero_copy = true;
+        p.zc_ok = all_fast && build_forward_ooc_ex(p, p.zc, p.budget, zo);
+    }
     int64_t cin, cx, cy, co;
     forward_caps(p, &cin, &cx, &cy, &co);
     p.ring_planes = cin;

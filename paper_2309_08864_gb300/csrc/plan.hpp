@@ -49,6 +49,8 @@ struct Op {
     int aux3_buf = -1;
     int64_t aux3_lo = 0, aux3_slot0 = 0;
     int64_t arg0 = 0, arg1 = 0, arg2 = 0;  // kernel-specific integers
+    int host_src = -1;      // zero-copy kernels: host array whose planes [host_lo, host_hi) they read
+    int64_t host_lo = 0, host_hi = 0;
     bool waited = false;    // some later op waits on this op's completion event
 };
 
@@ -101,6 +103,8 @@ struct Plan {
     RunList ooc, ic;
     RunList rr;                       // redundancy-free comparison code (result reuse), if it fits
     int rr_chunks = 0;
+    RunList zc;                       // zero-copy input (run mode 3), if the 3D star kernel runs every first launch
+    bool zc_ok = false;
     double redundancy = 0.0;
     int max_kon = kMaxKon;            // deepest fused launch the kernels support
     int lookahead = 1;                // circular buffer holds the next chunk's new planes too (1) or not (0)
@@ -163,6 +167,10 @@ struct ForwardOpts {
     // round 0 only, single-step launches: host array receiving the state after
     // launch j (j = 0 .. k'-2; the last state goes to dst_array[0])
     std::vector<int> state_array;
+    // zero-copy input: no host-to-device copy of the grid; the first launch of
+    // each chunk reads the chunk's new planes from the mapped host grid and
+    // writes them into the circular buffer for the next chunk
+    bool zero_copy = false;
 };
 
 // Forward op list with per-round source/destination host arrays.

@@ -206,6 +206,14 @@ int enqueue_stencil(so2dr_plan_s* P, const RunList& rl, const Op& op, cudaStream
     a.tx = ls.tx;
     a.ty = ls.ty;
     a.status = reinterpret_cast<int*>(P->arena + rl.arena_bytes - kAlign);  // the run list's status word
+    if (op.host_src >= 0) {
+        // zero-copy input: the device mapping of the host array
+        if (op.host_src >= (int)P->host_dev.size() || !P->host_dev[op.host_src])
+            return set_error(SO2DR_E_DEVICE_CHECK, "zero-copy launch without a mapped host grid");
+        a.host_in = P->host_dev[op.host_src];
+        a.host_lo = op.host_lo;
+        a.host_hi = op.host_hi;
+    }
     for (size_t k = 0; k < p.coeffs.size() && k < (size_t)kMaxCoeffsDev; ++k) {
         a.c[k] = p.coeffs[k];
         a.cf[k] = (float)p.coeffs[k];
@@ -406,7 +414,7 @@ int plan_create(so2dr_plan_t* out, int ndim, const int64_t* dims, int radius, in
 
 extern "C" {
 
-int so2dr_abi_version(void) { return 4; }
+int so2dr_abi_version(void) { return 5; }
 
 const char* so2dr_strerror(int status) {
     switch (status) {
@@ -487,6 +495,7 @@ int so2dr_plan_info(so2dr_plan_t P, so2dr_plan_info_t* info) {
     info->out_slabs = p.n_out;
     info->arena_bytes_result_reuse = p.rr_chunks ? p.rr.arena_bytes : 0;
     info->result_reuse_chunks = p.rr_chunks;
+    info->zero_copy = p.zc_ok ? 1 : 0;
     return SO2DR_OK;
 }
 
@@ -512,7 +521,7 @@ int so2dr_plan_chunks(so2dr_plan_t P, int64_t* starts, int max_entries) {
 
 int so2dr_plan_ops(so2dr_plan_t P, int in_core, so2dr_op_t* ops, int64_t max_ops, int64_t* n_ops) {
     if (!P || !n_ops) return set_error(SO2DR_E_INVAL, "NULL argument");
-    const RunList& rl = in_core == 2 ? P->p.rr : (in_core ? P->p.ic : P->p.ooc);
+    const RunList& rl = in_core == 3 ? P->p.zc : in_core == 2 ? P->p.rr : (in_core ? P->p.ic : P->p.ooc);
     *n_ops = (int64_t)rl.ops.size();
     if (!ops) return SO2DR_OK;
     if (max_ops < *n_ops) return set_error(SO2DR_E_INVAL, "ops array too small");
@@ -522,7 +531,7 @@ int so2dr_plan_ops(so2dr_plan_t P, int in_core, so2dr_op_t* ops, int64_t max_ops
 
 int so2dr_plan_buffers(so2dr_plan_t P, int in_core, so2dr_buffer_t* bufs, int max_bufs, int* n_bufs) {
     if (!P || !n_bufs) return set_error(SO2DR_E_INVAL, "NULL argument");
-    const RunList& rl = in_core == 2 ? P->p.rr : (in_core ? P->p.ic : P->p.ooc);
+    const RunList& rl = in_core == 3 ? P->p.zc : in_core == 2 ? P->p.rr : (in_core ? P->p.ic : P->p.ooc);
     *n_bufs = (int)rl.bufs.size();
     if (!bufs) return SO2DR_OK;
     if (max_bufs < *n_bufs) return set_error(SO2DR_E_INVAL, "bufs array too small");
@@ -591,10 +600,19 @@ int so2dr_run(so2dr_plan_t P, void* host_grid, const void* host_coeff_fields, in
         rc = check_pinned(host_coeff_fields, "host_coeff_fields");
         if (rc) return rc;
     }
-    if (in_core < 0 || in_core > 2) return set_error(SO2DR_E_INVAL, "mode must be 0, 1 or 2");
+    if (in_core < 0 || in_core > 3) return set_error(SO2DR_E_INVAL, "mode must be 0, 1, 2 or 3");
     if (in_core == 2 && p.rr_chunks == 0)
         return set_error(SO2DR_E_UNSUPPORTED, "the result-reuse code needs a constant-coefficient plan that fits");
-    const RunList& rl = in_core == 2 ? p.rr : (in_core ? p.ic : p.ooc);
+    if (in_core == 3 && !p.zc_ok)
+        return set_error(SO2DR_E_UNSUPPORTED, "zero-copy input needs a 3D constant-coefficient star on the 3D star kernel");
+    const RunList& rl = in_core == 3 ? p.zc : in_core == 2 ? p.rr : (in_core ? p.ic : p.ooc);
+    P->host_dev.assign(1, nullptr);
+    if (in_core == 3) {
+        void* d = nullptr;
+        cudaError_t e = cudaHostGetDevicePointer(&d, host_grid, 0);
+        if (e != cudaSuccess || !d) return cuda_fail(e, "cudaHostGetDevicePointer(host_grid)");
+        P->host_dev[0] = static_cast<char*>(d);
+    }
     char* hosts[2] = {static_cast<char*>(host_grid), const_cast<char*>(static_cast<const char*>(host_coeff_fields))};
     int64_t cb = p.dtype == SO2DR_F64 ? 8 : 4;
     int64_t hpb[2] = {p.plane_bytes, p.plane_cells * cb};

@@ -23,6 +23,7 @@ struct so2dr_plan_s {
     int sm_count = 0;
     int occ_cache[2][17] = {};      // CTAs per SM of the fast / generic launch per depth
     std::vector<double> tl_start, tl_end;  // per-op times of the last timed op list (ms from its start)
+    std::vector<char*> host_dev;    // device mappings of the run's host arrays (zero-copy input)
 
     ~so2dr_plan_s();
     void unbind();

@@ -113,6 +113,8 @@ struct StarTB {
     bool xl, xr;          // my lane holds column 0 / column nx-1 of the grid
     unsigned inyx;        // bit y*4+e: my cell (row y, column e) is interior in its plane
     T* out;
+    const T* hin;         // zero-copy: mapped host grid (planes [hlo, hhi) come from there)
+    int hlo, hhi;
     float2 A[K][W2][VY][2];                 // 2R partial sums per cell per level, in x pairs
     float2 C[K > 1 ? K - 1 : 1][VY][2];     // my cells of what levels 0..K-2 completed last phase
 
@@ -139,6 +141,44 @@ struct StarTB {
         const uint32_t bar = bar0 + (uint32_t)(q % NI) * 8u;
         mbar_arrive_expect_tx(bar, (uint32_t)S::template box_bytes<ES>());
         tma_load_3d(sin0 + (uint32_t)(q % NI) * SLOT, tmap, bx0, ys - R, slot, bar);
+    }
+
+    // zero-copy input: plane z comes from the mapped host grid
+    __device__ __forceinline__ bool host_plane(int z) const { return z < zb && z >= hlo && z < hhi; }
+
+    // all threads: 16-byte cp.async copies of the box of phase q (the same
+    // rows and columns the TMA box covers, zeros outside the grid) from the
+    // mapped host grid into its slot
+    __device__ __forceinline__ void stage_host(int q) {
+        constexpr int VEC = 16 / ES, NV = LXB / VEC;
+        const int z = za + q;
+        const T* base = hin + (int64_t)z * plane;
+        T* sb = const_cast<T*>(sin) + (q % NI) * (SLOT / ES);
+        for (int v = threadIdx.x; v < ROWS * NV; v += S::NT) {
+            const int row = v / NV, cv = v - row * NV;
+            const int gy = ys - R + row, gx = bx0 + cv * VEC;
+            const bool ok = gy >= 0 && gy < ny && gx >= 0 && gx < nx;
+            cp_async16(sb + row * LXB + cv * VEC, ok ? base + (int64_t)gy * nx + gx : base, ok);
+        }
+    }
+
+    // all threads: the tile's own part of the host plane of phase p (rows
+    // [y0, y0 + TY), columns [x0, x0 + TX): the tiles partition the plane) goes
+    // into the input buffer, where later launches read it
+    __device__ __forceinline__ void write_back(int p) {
+        constexpr int VEC = 16 / ES, NV = S::TX / VEC;
+        const int z = za + p;
+        const int slot = (int)((a.in_slot0 + (int64_t)(z - (int)a.in_lo)) % a.in_cap);
+        T* dst = const_cast<T*>(static_cast<const T*>(a.in)) + (int64_t)slot * plane;
+        const T* sb = sin + (p % NI) * (SLOT / ES);
+        const int x0 = xs + S::HXA, y0 = ys + S::HY;
+        for (int v = threadIdx.x; v < S::TY * NV; v += S::NT) {
+            const int r = v / NV, cv = v - r * NV;
+            const int gy = y0 + r, gx = x0 + cv * VEC;
+            if (gy < ny && gx < nx)
+                *reinterpret_cast<uint4*>(dst + (int64_t)gy * nx + gx) =
+                    *reinterpret_cast<const uint4*>(sb + (gy - ys + R) * LXB + (gx - bx0));
+        }
     }
 
     // keep (boundary) or nv, per element of a pair: per-cell mask bits
@@ -327,16 +367,22 @@ struct StarTB {
     __device__ __forceinline__ bool phase(int p0) {
         const int p = p0 + PH;
         bool late = false;
-        if (za + p < zb) late = !mbar_wait_bounded(bar0 + (uint32_t)(p % NI) * 8u, (uint32_t)((p / NI) & 1));
+        const bool hp = host_plane(za + p);
+        if (hp) cp_async_wait_group<PD - 1>();  // one group per phase: this phase's has landed
+        else if (za + p < zb) late = !mbar_wait_bounded(bar0 + (uint32_t)(p % NI) * 8u, (uint32_t)((p / NI) & 1));
         if (__syncthreads_or(late)) {
             pfail = p;
             return false;
         }
+        if (hp) write_back(p);
         // the slot of phase p + PD last held phase p - 1, read before the barrier
-        if (threadIdx.x == 0) {
+        if (host_plane(za + p + PD)) {
+            stage_host(p + PD);
+        } else if (threadIdx.x == 0) {
             fence_proxy_async_smem();
             issue(p + PD);
         }
+        cp_async_commit();
         // the arrivals of this phase span planes za + p - (K-1)(R+1) .. za + p;
         // a fixed plane among their targets (z' - R .. z') needs the cell path
         const bool all = p >= ps_lo && p < ps_hi;
@@ -379,6 +425,9 @@ struct StarTB {
         bx0 = ES == 4 ? xs : (xs & ~7);  // 16-byte aligned box start
         col0 = (xs - bx0) + lane * 4;
         out = static_cast<T*>(a.out);
+        hin = static_cast<const T*>(a.host_in);
+        hlo = hin ? (int)a.host_lo : 0;
+        hhi = hin ? (int)a.host_hi : 0;
         inyx = 0;
 #pragma unroll
         for (int y = 0; y < VY; ++y)
@@ -443,8 +492,11 @@ struct StarTB {
             fence_mbar_init();
         }
         __syncthreads();
-        if (threadIdx.x == 0)
-            for (int q = 0; q < PD; ++q) issue(q);
+        for (int q = 0; q < PD; ++q) {
+            if (host_plane(za + q)) stage_host(q);
+            else if (threadIdx.x == 0) issue(q);
+            cp_async_commit();
+        }
         bool ok = true;
         for (int p0 = 0; p0 < nph && ok; p0 += W2) ok = phase<0>(p0);
         if (!ok) {
@@ -454,10 +506,12 @@ struct StarTB {
                 if (a.status) atomicOr(a.status, 1);
                 // phases pfail .. pfail + PD - 1 were issued and not consumed
                 for (int q = pfail; q < pfail + PD && za + q < zb; ++q)
-                    (void)mbar_wait_bounded(bar0 + (uint32_t)(q % NI) * 8u, (uint32_t)((q / NI) & 1));
+                    if (!host_plane(za + q))
+                        (void)mbar_wait_bounded(bar0 + (uint32_t)(q % NI) * 8u, (uint32_t)((q / NI) & 1));
             }
             __syncthreads();
         }
+        cp_async_wait_all();  // no cp.async copy outlives the CTA
     }
 };
 

@@ -19,7 +19,17 @@ template <typename T> __device__ __forceinline__ void cp_async_vec4(T* sdst, con
     else
         asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(sa), "l"(gsrc), "r"(n));
 }
+// 16 bytes from global (device or mapped host) memory to shared memory;
+// zero-filled when !valid
+__device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc, bool valid) {
+    unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
+    int n = valid ? 16 : 0;
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(gsrc), "r"(n));
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N> __device__ __forceinline__ void cp_async_wait_group() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
 // four consecutive storage elements -> FP32

@@ -45,7 +45,8 @@ class PlanInfo(ctypes.Structure):
                 ("h2d_bytes_per_run", ctypes.c_double), ("d2h_bytes_per_run", ctypes.c_double),
                 ("cell_updates_per_run", ctypes.c_double), ("redundancy", ctypes.c_double),
                 ("lookahead", ctypes.c_int), ("out_slabs", ctypes.c_int),
-                ("arena_bytes_result_reuse", ctypes.c_size_t), ("result_reuse_chunks", ctypes.c_int)]
+                ("arena_bytes_result_reuse", ctypes.c_size_t), ("result_reuse_chunks", ctypes.c_int),
+                ("zero_copy", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):

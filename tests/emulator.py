@@ -12,6 +12,21 @@ import numpy as np
 import oracle
 
 
+def _new_planes(plan, o):
+    """Planes the first launch of a chunk reads from the host grid in the
+    zero-copy mode (run mode 3): the chunk's new planes of its round."""
+    info = plan.info
+    starts = plan.chunks()
+    n0, r, T, k_off = info["dims"][0], info["radius"], info["time_steps"], info["k_off"]
+    t, i = o["round"], o["chunk"]
+    rounds = -(-T // k_off)
+    kk = T % k_off if (t == rounds - 1 and T % k_off) else k_off
+    s, e = starts[i], starts[i + 1]
+    lo = 0 if i == 0 else min(n0, s + r * kk)
+    hi = n0 if i == len(starts) - 2 else min(n0, e + r * kk)
+    return lo, hi
+
+
 def replay(plan, u0, coeff_fields=None, in_core=False, seed=0, policy="random"):
     info = plan.info
     nd = info["ndim"]
@@ -54,6 +69,12 @@ def replay(plan, u0, coeff_fields=None, in_core=False, seed=0, policy="random"):
         else:
             lo, hi = o["src_lo"], o["src_hi"]
             b = o["src_buf"]
+            if int(in_core) == 3 and b == 0:
+                # zero-copy input: the launch reads the chunk's new planes from
+                # the host grid and writes them into the circular buffer
+                nlo, nhi = _new_planes(plan, o)
+                if nhi > nlo:
+                    dev[0][slots(o["src_slot0"] + (nlo - lo), nhi - nlo, bufs[0][1])] = host[nlo:nhi]
             sub = dev[b][slots(o["src_slot0"], hi - lo, bufs[b][1])]
             depth = o["depth"]
             # the valid range of the last fused level must cover the output

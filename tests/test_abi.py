@@ -30,7 +30,7 @@ def test_library_builds_and_exports_every_declared_symbol():
 
 def test_version_and_status_strings():
     lib = so2dr.load_library()
-    assert lib.so2dr_abi_version() == 4
+    assert lib.so2dr_abi_version() == 5
     for code in range(0, -10, -1):
         s = lib.so2dr_strerror(code).decode()
         assert s and s != "unknown status"

@@ -130,3 +130,46 @@ def test_result_reuse_code_is_exact(case):
     for sd in (0, 1):
         assert np.array_equal(replay(p, u0, None, in_core=2, seed=sd), ref)
     assert np.array_equal(replay(p, u0, None, in_core=2, policy="h2d_first"), ref)
+
+
+ZC_CASES = [
+    # dims, r, T, min_chunks, k_on, k_off, dtype
+    ((70, 12, 16), 1, 11, 7, 4, 8, "f32"),     # residual round, ragged chunks
+    ((71, 13, 16), 1, 19, 3, 4, 19, "f32"),    # one round
+    ((64, 14, 16), 2, 9, 5, 2, 4, "bf16"),     # radius 2, 16-bit storage
+    ((40, 8, 8), 1, 10, 38, 2, 10, "f32"),     # one plane per chunk, P << 2rk
+    ((60, 10, 16), 4, 5, 3, 1, 3, "f32"),      # radius 4
+]
+
+
+@pytest.mark.parametrize("case", ZC_CASES)
+def test_zero_copy_replay_is_bit_identical_to_in_core_oracle(case):
+    """Run mode 3 (zero-copy input): no host-to-device copy of the grid; the
+    first launch of each chunk reads its new planes from the host grid and
+    writes them into the circular buffer for the next chunk.  Any interleaving
+    the waits allow gives the in-core result, and the in-place host grid is
+    read only after the previous round wrote it back."""
+    dims, r, T, dmin, kon, koff, dtype = case
+    c, _ = _setup(dims, r, "star")
+    p = so2dr.Plan(dims, r, "star", c, T, min_chunks=dmin, k_on=kon, k_off=koff, budget_bytes=0, dtype=dtype)
+    assert p.info["zero_copy"] == 1
+    ops = p.ops(3)
+    assert not any(o["kind"] == 0 for o in ops)   # no host-to-device copy at all
+    u0 = inputs.draw_box(1, dims)
+    ref = oracle.run(u0, c, r, 0, T)
+    for sd in (0, 1, 2):
+        assert np.array_equal(replay(p, u0, None, in_core=3, seed=sd), ref), sd
+    for pol in ("h2d_first", "d2h_first"):
+        assert np.array_equal(replay(p, u0, None, in_core=3, policy=pol), ref), pol
+
+
+def test_zero_copy_needs_the_3d_star_kernel():
+    p = so2dr.Plan((48, 40), 1, "star", [0.2] * 5, 8, min_chunks=3, k_on=2, k_off=4, dtype="f32")
+    assert p.info["zero_copy"] == 0   # 2D: the generic kernel
+    p = so2dr.Plan((40, 12, 16), 1, "star", C7_STAR, 8, min_chunks=3, k_on=2, k_off=4, dtype="f64")
+    assert p.info["zero_copy"] == 0   # FP64 storage: the generic kernel
+    p = so2dr.Plan((40, 12, 18), 1, "star", C7_STAR, 8, min_chunks=3, k_on=2, k_off=4, dtype="f32")
+    assert p.info["zero_copy"] == 0   # rows of 18 FP32 values are not a whole number of 16 bytes
+
+
+C7_STAR = [0.4] + [0.1] * 6
