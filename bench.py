@@ -471,9 +471,6 @@ def run_adjoint(args, cfg, world, rank, local):
     value = world * cells * args.steps / (ms * 1e-3) / 1e9
     h2d = stats[-1]["h2d_bytes"]
     d2h = stats[-1]["d2h_bytes"]
-    if mode == 3:
-        # zero-copy input: the first launches read the new planes over the link
-        h2d = info["h2d_bytes_per_run"]
     line = {"metric": "Gcell-updates/s out-of-core on 1 GB300 (forward + adjoint updates)", "value": value,
             "unit": "Gcell/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,

@@ -176,6 +176,11 @@ typedef struct {
  *   SO2DR_ALLOW_PAGEABLE  any value: skip the page-locked check on host
  *                         grids (copies from pageable memory are staged by
  *                         the driver and run slower).
+ *   SO2DR_ADJOINT_STEPS=K backward steps per adjoint round (or the largest
+ *                         K below it that fits the arena; default: chosen).
+ * A kernel whose bounded wait for a staged plane gives up (after about two
+ * seconds) sets the run list's device status word; so2dr_run then returns
+ * SO2DR_E_TIMEOUT.
  */
 
 /* ---------------------------------------------------------------- planning */
@@ -374,8 +379,12 @@ int so2dr_measure_link(void* host_a, void* host_b, void* device_arena, size_t by
  * Gradient of L = 1/2 ||u_T - u*||^2 (T = time_steps) for a VARCOEF_STAR plan,
  * through the same out-of-core pipeline: a forward sweep that keeps u every
  * checkpoint_every steps in host_workspace, then, segment by segment from the
- * last, recomputation of the segment's states and the transposed stencil run
- * backward in time, accumulating dL/dc_f on the cells each chunk owns.
+ * last, recomputation of the segment's states (one round of single-step
+ * launches that sends every state back) and the transposed stencil run
+ * backward in time in rounds of K steps (K <= checkpoint_every, the largest
+ * worth it under the budget; SO2DR_ADJOINT_STEPS pins it), accumulating
+ * dL/dc_f of a round's K steps on the cells each chunk owns before it goes
+ * back to the host.
  *   host_u0, host_coeff_fields, host_target   inputs (read-only).
  *   host_grad_u0     out: dL/du_0 for every cell (N elements, plan dtype).
  *   host_grad_coeffs out: dL/dc_f, [6][N] in the compute type; zero off I.

@@ -89,7 +89,7 @@ enum BndMode : int {
     kBndCells = 2,    // boundary rows or fixed planes: per-cell masks
 };
 
-template <typename T, int R, int K>
+template <typename T, int R, int K, bool ZC>
 struct StarTB {
     using S = StarShape<R, K>;
     static constexpr int VY = S::VY, NW = S::NW, LX = S::LX, LYT = S::LYT, ROWS = S::ROWS, NI = S::NI,
@@ -363,26 +363,9 @@ struct StarTB {
     }
 
     // phase p = p0 + PH; false when an input copy did not land in time
+    // the levels of phase p (PH = p mod 2R)
     template <int PH>
-    __device__ __forceinline__ bool phase(int p0) {
-        const int p = p0 + PH;
-        bool late = false;
-        const bool hp = host_plane(za + p);
-        if (hp) cp_async_wait_group<PD - 1>();  // one group per phase: this phase's has landed
-        else if (za + p < zb) late = !mbar_wait_bounded(bar0 + (uint32_t)(p % NI) * 8u, (uint32_t)((p / NI) & 1));
-        if (__syncthreads_or(late)) {
-            pfail = p;
-            return false;
-        }
-        if (hp) write_back(p);
-        // the slot of phase p + PD last held phase p - 1, read before the barrier
-        if (host_plane(za + p + PD)) {
-            stage_host(p + PD);
-        } else if (threadIdx.x == 0) {
-            fence_proxy_async_smem();
-            issue(p + PD);
-        }
-        cp_async_commit();
+    __device__ __forceinline__ void phase_levels(int p) {
         // the arrivals of this phase span planes za + p - (K-1)(R+1) .. za + p;
         // a fixed plane among their targets (z' - R .. z') needs the cell path
         const bool all = p >= ps_lo && p < ps_hi;
@@ -401,6 +384,37 @@ struct StarTB {
             else if (wmode == kBndColumns) levels<K - 1, PH, kBndColumns, false>(p, all);
             else levels<K - 1, PH, kBndNone, false>(p, all);
         }
+    }
+
+    // phase p = p0 + PH: its input plane has landed (bounded wait), the
+    // barrier, (zero-copy: the write-back of a host plane,) the copy of plane
+    // p + PD, then the levels; false when an input copy did not land in time
+    template <int PH>
+    __device__ __forceinline__ bool phase(int p0) {
+        const int p = p0 + PH;
+        bool late = false;
+        bool hp = false;
+        if constexpr (ZC) hp = host_plane(za + p);
+        if (hp) cp_async_wait_group<PD - 1>();  // one group per phase: this phase's has landed
+        else if (za + p < zb) late = !mbar_wait_bounded(bar0 + (uint32_t)(p % NI) * 8u, (uint32_t)((p / NI) & 1));
+        if (__syncthreads_or(late)) {
+            pfail = p;
+            return false;
+        }
+        // the slot of phase p + PD last held phase p - 1, read before the barrier
+        if constexpr (ZC) {
+            if (hp) write_back(p);
+            if (host_plane(za + p + PD)) stage_host(p + PD);
+            else if (threadIdx.x == 0) {
+                fence_proxy_async_smem();
+                issue(p + PD);
+            }
+            cp_async_commit();
+        } else if (threadIdx.x == 0) {
+            fence_proxy_async_smem();
+            issue(p + PD);
+        }
+        phase_levels<PH>(p);
         if constexpr (PH + 1 < W2) return phase<PH + 1>(p0);
         return true;
     }
@@ -426,8 +440,8 @@ struct StarTB {
         col0 = (xs - bx0) + lane * 4;
         out = static_cast<T*>(a.out);
         hin = static_cast<const T*>(a.host_in);
-        hlo = hin ? (int)a.host_lo : 0;
-        hhi = hin ? (int)a.host_hi : 0;
+        hlo = ZC && hin ? (int)a.host_lo : 0;
+        hhi = ZC && hin ? (int)a.host_hi : 0;
         inyx = 0;
 #pragma unroll
         for (int y = 0; y < VY; ++y)
@@ -493,9 +507,13 @@ struct StarTB {
         }
         __syncthreads();
         for (int q = 0; q < PD; ++q) {
-            if (host_plane(za + q)) stage_host(q);
-            else if (threadIdx.x == 0) issue(q);
-            cp_async_commit();
+            if constexpr (ZC) {
+                if (host_plane(za + q)) stage_host(q);
+                else if (threadIdx.x == 0) issue(q);
+                cp_async_commit();
+            } else if (threadIdx.x == 0) {
+                issue(q);
+            }
         }
         bool ok = true;
         for (int p0 = 0; p0 < nph && ok; p0 += W2) ok = phase<0>(p0);
@@ -506,20 +524,23 @@ struct StarTB {
                 if (a.status) atomicOr(a.status, 1);
                 // phases pfail .. pfail + PD - 1 were issued and not consumed
                 for (int q = pfail; q < pfail + PD && za + q < zb; ++q)
-                    if (!host_plane(za + q))
+                    if (!ZC || !host_plane(za + q))
                         (void)mbar_wait_bounded(bar0 + (uint32_t)(q % NI) * 8u, (uint32_t)((q / NI) & 1));
             }
             __syncthreads();
         }
-        cp_async_wait_all();  // no cp.async copy outlives the CTA
+        if constexpr (ZC) cp_async_wait_all();  // no cp.async copy outlives the CTA
     }
 };
 
-template <typename T, int R, int K>
+// ZC: the launch reads some input planes from the mapped host grid (zero-copy
+// input); a separate instantiation, so that the launches of the copy-engine
+// pipeline carry none of its code
+template <typename T, int R, int K, bool ZC = false>
 __global__ void __launch_bounds__(StarShape<R, K>::NT, StarShape<R, K>::MINB)
     star3d_tb_kernel(const StencilArgs a, const __grid_constant__ CUtensorMap tmap) {
     extern __shared__ __align__(1024) unsigned char smem_tb[];
-    StarTB<T, R, K> k(a, &tmap);
+    StarTB<T, R, K, ZC> k(a, &tmap);
     k.run(smem_tb);
 }
 

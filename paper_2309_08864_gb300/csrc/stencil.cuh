@@ -41,15 +41,15 @@ struct StencilArgs {
     int lx, ly;           // loaded tile, halo included
     int tx, ty;           // output tile
     int* status;          // device status word (index checks)
+    double c[kMaxCoeffsDev];
+    float cf[kMaxCoeffsDev];   // the same weights rounded once to FP32
+    float2 cf2[kMaxCoeffsDev]; // (cf, cf) pairs for packed FP32x2 FMAs
     // zero-copy input (3D star kernel): planes [host_lo, host_hi) are read
     // from host_in (mapped pinned host memory, plane z at host_in + z * plane)
     // instead of the input buffer, and written into the input buffer for the
     // launches that read them later
     const void* host_in;
     int64_t host_lo, host_hi;
-    double c[kMaxCoeffsDev];
-    float cf[kMaxCoeffsDev];   // the same weights rounded once to FP32
-    float2 cf2[kMaxCoeffsDev]; // (cf, cf) pairs for packed FP32x2 FMAs
 };
 
 template <typename T> struct Compute { using type = float; };
