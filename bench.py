@@ -52,7 +52,13 @@ KERNEL_SRC = {"star": os.path.join(ROOT, "paper_2309_08864_gb300", "csrc", "star
 # summaries under profiles/ give the commands), keyed by the first 16 hex
 # digits of the SHA-256 of the kernel source they were taken with: a capture
 # of an older kernel is not reported.
-DRAM_TRAFFIC = {}
+# Captured launches are one run's middle chunks; the figure is their DRAM
+# bytes per input+output plane times the mean input+output planes of all of
+# the plan's k_on-deep launches (edge chunks clip their trapezoids).
+DRAM_TRAFFIC = {
+    # config: (k_off, k_on of the captured plan, bytes per launch)
+    "9644aedcf04aa295": {"c2": (22, 4, 453.0e6), "c3": (8, 1, 1557.9e6)},
+}
 # host-link bandwidths measured earlier on the GB300 machines with pinned
 # buffers (cudaMemcpyAsync, 4 GiB): host-to-device 211, device-to-host 193,
 # both directions at once 343 GB/s in total; reported beside the rates the
@@ -605,7 +611,8 @@ def bench_config(args, cfg, name, world, rank, local, torch, inputs, so2dr, link
     achieved_tf = alg_flops_per_launch / avg_launch_s / 1e12 if mk_n else 0.0
     alu_bound = alg_flops_per_launch / (ALU_PEAK_TFLOPS * 1e12) > alg_bytes_per_launch / (hbm_peak * 1e9)
     kind = cfg.get("kind", "star")
-    traffic = DRAM_TRAFFIC.get(source_digest(KERNEL_SRC[kind]), {}).get(name) if mode == 0 else None
+    cap = DRAM_TRAFFIC.get(source_digest(KERNEL_SRC[kind]), {}).get(name) if mode == 0 else None
+    traffic = cap[2] if cap and (cap[0], cap[1]) == (info["k_off"], info["k_on"]) else None
     # whole-path roofline: max(host-link time, HBM time) of the algorithmic
     # bytes (every cell sent and received once per round; two HBM passes for
     # the transfers and two per fused launch), against the link measured above
@@ -614,6 +621,12 @@ def bench_config(args, cfg, name, world, rank, local, torch, inputs, so2dr, link
     for e in cfg["dims"]:
         Nb *= e
     pr = path_roofline(Nb, info["rounds"], -(-info["k_off"] // info["k_on"]), link, hbm_peak)
+    if mode == 1:
+        # in-core: no host traffic inside the run; one read and one write of
+        # the grid per k_on-deep launch
+        hb = 2.0 * Nb * -(-cfg["T"] // info["k_on"])
+        pr = {"t_roof_s": hb / (hbm_peak * 1e9), "t_link_s": 0.0, "t_hbm_s": hb / (hbm_peak * 1e9),
+              "hbm_bytes": hb, "bound": "hbm"}
     # the same against the fewest rounds the budget admits (largest feasible
     # k_off), so that plans with different round counts read on one scale
     cand = so2dr.candidates(cfg["dims"], cfg["r"], kind, coeffs, cfg["T"], min_chunks=cfg["min_chunks"],
@@ -647,9 +660,11 @@ def bench_config(args, cfg, name, world, rank, local, torch, inputs, so2dr, link
                           "frac": pr["t_roof_s"] / t_meas, "frac_vs_measured_link": pr["t_roof_s"] / t_meas,
                           "link_measured_gbs": {k: link[k] for k in ("ce_h2d", "ce_d2h", "ce_both_h2d",
                                                                      "ce_both_d2h")},
-                          "frac_min_rounds": prm["t_roof_s"] / t_meas, "min_rounds": rmin, "k_off_max": kmax,
-                          "frac_vs_pool_link": t_pool / t_meas, "link_pool_bidir_gbs": LINK_BIDIR_GBS,
-                          "host_bytes": 2.0 * Nb * info["rounds"], "hbm_bytes": pr["hbm_bytes"], "hbm_gbs": hbm_peak,
+                          "frac_min_rounds": prm["t_roof_s"] / t_meas if mode != 1 else None,
+                          "min_rounds": rmin, "k_off_max": kmax,
+                          "frac_vs_pool_link": t_pool / t_meas if mode != 1 else None,
+                          "link_pool_bidir_gbs": LINK_BIDIR_GBS,
+                          "host_bytes": 2.0 * Nb * info["rounds"] if mode != 1 else 0.0, "hbm_bytes": pr["hbm_bytes"], "hbm_gbs": hbm_peak,
                           "stream_gbs_during_run": {"h2d": (stats[-1]["h2d_bytes"] / (stats[-1]["h2d_ms"] * 1e-3) / 1e9
                                                             if stats[-1]["h2d_ms"] > 0 else None),
                                                     "d2h": (d2h / (stats[-1]["d2h_ms"] * 1e-3) / 1e9
@@ -663,6 +678,8 @@ def bench_config(args, cfg, name, world, rank, local, torch, inputs, so2dr, link
                      "alu": {"achieved_tflops": achieved_tf, "peak_tflops": ALU_PEAK_TFLOPS,
                              "frac": achieved_tf / ALU_PEAK_TFLOPS, "flop_per_cell_step": 2 * npts - 1},
                      "traffic": traffic,
+                     # above 1 by the redundant trapezoid planes a launch also computes
+                     "traffic_vs_alg": traffic / alg_bytes_per_launch if traffic and alg_bytes_per_launch else None,
                      "kernel": ("box2d_fast_kernel" if kind == "box" else "star3d_tb_kernel")
                                + " (k_on-step TB launch)", "peak_kind": ("derived from unit counts and the maximum SM clock" if alu_bound
                                    else peak_kind + " (burst)"),

@@ -46,6 +46,11 @@ template <int R, int K> struct BoxShape {
     static constexpr int PD = 4;                       // input rows staged ahead
     static constexpr int NBI = R + 1 + PD;             // input row slots
     template <int ES> static constexpr int smem() { return NBI * ROW * ES + NB * (K - 1) * ROW * 4; }
+    // two CTAs per SM (at most 128 registers a thread), so that one CTA's
+    // barrier waits are hidden by the other's work; radius >= 3 at R*K >= 8
+    // would spill under that cap and keeps one
+    static constexpr int MINB = (R >= 3 && R * K >= 8) ? 1 : 2;
+    static_assert(MINB == 1 || 2 * (smem<4>() + 1024) <= 228 * 1024, "two CTAs must fit an SM's shared memory");
 };
 
 template <typename T, int R, int K>
@@ -64,6 +69,7 @@ struct FastBox {
     T* sin;       // [NBI][ROW] staged input rows (row of phase p in slot p % NBI)
     float* slev;  // [K-1][NB][ROW] completed rows of levels 0..K-2
     int tid, n0, nx, olo, ohi, need_lo, need_hi, xs, gx0, za, zb, slot_next;
+    int ps_lo, ps_hi;  // phases in which every level is active
     bool xin, warp_bnd;
     unsigned inx;  // bit e: my column e is an interior column
     const T* in;
@@ -179,12 +185,17 @@ struct FastBox {
 
     // level L of phase p (PH = p mod 2R): consumes input row za + p (L = 0)
     // or what level L-1 completed in phase p-1 (row za + p - L(R+1))
-    template <int L, int PH>
+    // (ALL: a phase in which every level is active, run as straight-line code)
+    template <int L, int PH, bool ALL>
     __device__ __forceinline__ void level(int p, const T* sbuf, int buf) {
-        const int zp = za + p - L * (R + 1);
-        const int lo = need_lo - (K - L) * R, hi = need_hi + (K - L) * R;
-        if (!(zp < za || zp < lo || zp >= hi)) level_body<L, PH>(p, sbuf, buf);
-        if constexpr (L + 1 < K) level<L + 1, PH>(p, sbuf, buf);
+        if constexpr (ALL) {
+            level_body<L, PH>(p, sbuf, buf);
+        } else {
+            const int zp = za + p - L * (R + 1);
+            const int lo = need_lo - (K - L) * R, hi = need_hi + (K - L) * R;
+            if (!(zp < za || zp < lo || zp >= hi)) level_body<L, PH>(p, sbuf, buf);
+        }
+        if constexpr (L + 1 < K) level<L + 1, PH, ALL>(p, sbuf, buf);
     }
 
     template <int L, int PH>
@@ -218,7 +229,8 @@ struct FastBox {
         // slot (p + PD) % NBI last held row p + PD - NBI = p - R - 1, whose
         // last reader (the level-0 fixup of phase p - 1) is behind the barrier
         stage_row(za + p + PD, (p + PD) % NBI);
-        level<0, PH>(p, sin + (p % NBI) * ROW, p % NB);
+        if (p >= ps_lo && p < ps_hi) level<0, PH, true>(p, sin + (p % NBI) * ROW, p % NB);
+        else level<0, PH, false>(p, sin + (p % NBI) * ROW, p % NB);
         if constexpr (PH + 1 < W2) phase<PH + 1>(p0);
     }
 
@@ -264,6 +276,19 @@ struct FastBox {
         olo = need_lo = zs;
         ohi = need_hi = ze;
         slot_next = (int)((a.in_slot0 + (za - in_lo)) % a.in_cap);
+        // phases in which every level is active: level L handles arrival
+        // za + p - L(R+1) in phase p, and needs arrivals from
+        // max(za, need_lo - (K-L)R) to need_hi + (K-L)R
+        ps_lo = 0;
+        ps_hi = 1 << 30;
+#pragma unroll
+        for (int L = 0; L < K; ++L) {
+            const int llo = need_lo - (K - L) * R;
+            const int lo = (llo > za ? llo : za) - za + L * (R + 1);
+            const int hi = need_hi + (K - L) * R - za + L * (R + 1);
+            ps_lo = lo > ps_lo ? lo : ps_lo;
+            ps_hi = hi < ps_hi ? hi : ps_hi;
+        }
         // last arrival any level needs: level K-1 at row need_hi + R - 1
         const int nph0 = (need_hi + R - 1 - za) + (K - 1) * (R + 1) + 1;
         const int nph = (nph0 + W2 - 1) / W2 * W2;
@@ -274,7 +299,7 @@ struct FastBox {
 };
 
 template <typename T, int R, int K>
-__global__ void __launch_bounds__(BoxShape<R, K>::NT, 1) box2d_fast_kernel(const StencilArgs a) {
+__global__ void __launch_bounds__(BoxShape<R, K>::NT, BoxShape<R, K>::MINB) box2d_fast_kernel(const StencilArgs a) {
     extern __shared__ float4 smem4[];
     FastBox<T, R, K> k(a);
     k.run(smem4);

@@ -346,7 +346,7 @@ int execute(so2dr_plan_s* P, const RunList& rl, char* const* hosts, const int64_
                 if (o.depth == (rr ? 1 : pp.k_on) && rl.ops[j].fn == kFnStencil) {
                     // algorithmic cells: the chunk's owned planes (the whole grid in-core;
                     // the launch's own output planes in the result-reuse code)
-                    int64_t owned = (&rl == &pp.ooc) ? pp.starts[o.chunk + 1] - pp.starts[o.chunk]
+                    int64_t owned = (&rl == &pp.ooc || &rl == &pp.zc) ? pp.starts[o.chunk + 1] - pp.starts[o.chunk]
                                                      : rr ? o.dst_hi - o.dst_lo : pp.n0;
                     stats->main_kernel_ms += d;
                     stats->main_kernel_launches += 1;
