@@ -186,8 +186,8 @@ typedef struct {
 /* ---------------------------------------------------------------- planning */
 
 /*
- * Builds a plan (host only; no CUDA call).  Algorithm 1's Require line gives
- * d, n, k_off and k_on; Table I adds the sizes and the device capacity.
+ * Builds a plan (host only; no CUDA call).  Algorithm 1 takes d, n, k_off
+ * and k_on as its inputs; Table I adds the sizes and the device capacity.
  *   ndim, dims     grid extents (ndim 2 or 3), boundary ring included.
  *   radius, kind   stencil radius r (1..4) and kind (see so2dr_kind).
  *   coeffs, ncoeffs constant-coefficient table (NULL/0 for VARCOEF_STAR).

@@ -3,7 +3,9 @@
 #include "box2d_fast.cuh"
 #include "star3d_tb.cuh"
 
+#include <cmath>
 #include <cstdlib>
+#include <cstring>
 
 namespace so2dr {
 
@@ -161,6 +163,41 @@ int choose_segments(int64_t tiles, int64_t nout, int r, int depth, int sms, int 
         if (n == 1 || cost < best_cost * 0.98) { best = n; best_cost = cost; }
     }
     return best;
+}
+
+void choose_work_split(LaunchShape& ls, int64_t nout, int r, int depth, int sms, int occ, int* split) {
+    *split = 0;
+    const int64_t tiles = (int64_t)ls.grid.x * ls.grid.y;
+    if (tiles <= 0 || nout <= 0 || sms <= 0) return;
+    const int nseg = choose_segments(tiles, nout, r, depth, sms, occ);
+    const double ovh = 2.0 * r * depth + depth;
+    const double cost_grid = (double)((tiles * nseg + sms - 1) / sms) * ((double)nout / nseg + ovh);
+    // round split: G = sms * occ CTAs take the tiles x n units in rounds;
+    // each unit of the last, partial round is cut into floor(G / rem) pieces
+    const int64_t occ1 = occ > 0 ? occ : 1, G = (int64_t)sms * occ1;
+    int best_n = 0;
+    double best = 0;
+    for (int n = 1; n <= 64 && n <= nout; ++n) {
+        const int64_t units = tiles * n, F = units / G, rem = units - F * G;
+        const double len = std::ceil((double)nout / n);
+        double cost = (double)F * (len + ovh);
+        if (rem) cost += std::ceil(len / (double)(G / rem)) + ovh;
+        cost *= (double)occ1;
+        if (best_n == 0 || cost < best * 0.98) { best_n = n; best = cost; }
+    }
+    const char* pin = std::getenv("SO2DR_WORK_SPLIT");
+    // (measured on GB300: the round split gains 4% on depth-4 launches and
+    // loses up to 9% on depth-2 ones, where the model rated it 7% better, so
+    // it is taken for fused depths of 3 and more only)
+    bool rounds = depth >= 3 && best < cost_grid * 0.97;
+    if (pin && std::strcmp(pin, "grid") == 0) rounds = false;
+    if (pin && std::strcmp(pin, "rounds") == 0) rounds = true;
+    if (rounds) {
+        ls.grid = dim3((unsigned)G, 1, 1);
+        *split = best_n;
+    } else {
+        ls.grid.z = (unsigned)nseg;
+    }
 }
 
 cudaError_t launch_stencil(int dtype, int shape, int r, const StencilArgs& a, const LaunchShape& ls,

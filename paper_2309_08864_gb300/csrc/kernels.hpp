@@ -55,6 +55,16 @@ int stencil_occupancy(int dtype, int shape, int r, int depth, const LaunchShape&
 // CTAs share the SM's throughput).
 int choose_segments(int64_t tiles, int64_t nout, int r, int depth, int sms, int occ);
 
+// Work split of a 3D star kernel launch (ls.grid is tiles in x by tiles in
+// y): either axis-0 segments per tile, one CTA each (choose_segments; *split
+// = 0, grid.z = segments), or sms * occ CTAs (a 1D grid) that take the tiles
+// x n (tile, segment) units in rounds, the units of the last, partial round
+// cut into shorter axis-0 pieces (*split = n), whichever the cost model
+// (busiest SM's CTAs times planes streamed, each piece paying the r * depth
+// halo each side and the depth-deep pipeline fill) rates cheaper by 3%, for
+// fused depths of 3 and more.  SO2DR_WORK_SPLIT=grid|rounds pins the choice.
+void choose_work_split(LaunchShape& ls, int64_t nout, int r, int depth, int sms, int occ, int* split);
+
 // Per-dtype instantiations (one translation unit each).
 int occupancy_stencil_f64(int shape, int r, int depth, const LaunchShape& ls);
 int occupancy_stencil_f32(int shape, int r, int depth, const LaunchShape& ls);

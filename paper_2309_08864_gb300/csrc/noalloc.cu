@@ -157,12 +157,13 @@ extern "C" int so2dr_run_device_noalloc(int ndim, const int64_t* dims, int radiu
         LaunchShape ls = stencil_launch_shape(shape, radius, depth, ny, nx, csize, (int)esize);
         if (!ls.ok) return set_error(SO2DR_E_UNSUPPORTED, "fused depth too large for the stencil kernel");
         ls.grid.z = 1;
-        if (ls.fast) {
-            int occ = stencil_occupancy(dtype, shape, radius, depth, ls);
-            ls.grid.z = (unsigned)choose_segments((int64_t)ls.grid.x * ls.grid.y, n0, radius, depth, sms, occ);
-        }
         StencilArgs a;
         std::memset(&a, 0, sizeof(a));
+        if (ls.fast) {
+            int occ = stencil_occupancy(dtype, shape, radius, depth, ls);
+            if (ls.fast == kFastStar3D) choose_work_split(ls, n0, radius, depth, sms, occ, &a.split);
+            else ls.grid.z = (unsigned)choose_segments((int64_t)ls.grid.x * ls.grid.y, n0, radius, depth, sms, occ);
+        }
         a.in = src;
         a.in_cap = n0;
         a.in_slot0 = 0;

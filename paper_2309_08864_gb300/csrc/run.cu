@@ -220,11 +220,15 @@ int enqueue_stencil(so2dr_plan_s* P, const RunList& rl, const Op& op, cudaStream
         a.cf2[k] = make_float2(a.cf[k], a.cf[k]);
     }
     if (ls.fast) {
-        // split axis 0 so the grid fills the SMs evenly
+        // split the work so that the grid fills the SMs evenly
         int& occ = P->occ_cache[1][o.depth];
         if (!occ) occ = stencil_occupancy(p.dtype, shape, p.r, o.depth, ls);
-        int64_t tiles = (int64_t)ls.grid.x * ls.grid.y;
-        ls.grid.z = (unsigned)choose_segments(tiles, o.dst_hi - o.dst_lo, p.r, o.depth, P->sm_count, occ);
+        if (ls.fast == kFastStar3D) {
+            choose_work_split(ls, o.dst_hi - o.dst_lo, p.r, o.depth, P->sm_count, occ, &a.split);
+        } else {
+            int64_t tiles = (int64_t)ls.grid.x * ls.grid.y;
+            ls.grid.z = (unsigned)choose_segments(tiles, o.dst_hi - o.dst_lo, p.r, o.depth, P->sm_count, occ);
+        }
     }
     cudaError_t e = launch_stencil(p.dtype, shape, p.r, a, ls, s);
     if (e != cudaSuccess) return cuda_fail(e, "stencil launch");

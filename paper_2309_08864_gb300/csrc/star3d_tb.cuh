@@ -4,9 +4,12 @@
 //
 // The on-chip temporal blocking of Sec. III / Sec. IV-A, laid out for sm_103a:
 //  * a CTA owns a 128-wide x tile (32 lanes x 4 cells) and NW*VY rows of y
-//    (VY rows per warp) and streams the planes of axis 0 through it; a launch
-//    may split axis 0 into segments (gridDim.z) so that the grid fills the
-//    SMs evenly;
+//    (VY rows per warp) and streams the planes of axis 0 through it.  The
+//    host picks the work split that loads the SMs most evenly: either one
+//    tile and one axis-0 segment per CTA (gridDim.z segments), or one CTA
+//    per SM slot taking (tile, segment) units in rounds, with the units of
+//    the last, partial round cut into shorter axis-0 pieces so that no SM
+//    idles while others finish a whole unit;
 //  * each input plane is read from device memory once, as one TMA box
 //    (cp.async.bulk.tensor, issued by one thread, landing on an mbarrier) of
 //    the tile plus R halo rows, PD planes ahead of its use in an NI-slot ring;
@@ -107,6 +110,8 @@ struct StarTB {
     int za, zb, olo, ohi, need_lo, need_hi;
     int ps_lo, ps_hi;     // phases in which every level is active
     int pfail;            // phase whose input copy did not land in time
+    int gb;               // input copies issued by this CTA before the current piece
+    unsigned par;         // bit s: parity of the next completion of mbarrier s
     int wmode;            // BndMode of my warp away from the fixed planes
     int64_t plane;
     bool xin;
@@ -134,13 +139,16 @@ struct StarTB {
     }
 
     // one thread: TMA of the input plane of phase q into its slot
+    // (the staging slot of phase q of a piece is (gb + q) mod NI: the slots
+    // go round in issue order across the pieces of a CTA)
     __device__ __forceinline__ void issue(int q) {
         const int z = za + q;
         if (z >= zb) return;
         const int slot = (int)((a.in_slot0 + (int64_t)(z - (int)a.in_lo)) % a.in_cap);
-        const uint32_t bar = bar0 + (uint32_t)(q % NI) * 8u;
+        const int g = (gb + q) % NI;
+        const uint32_t bar = bar0 + (uint32_t)g * 8u;
         mbar_arrive_expect_tx(bar, (uint32_t)S::template box_bytes<ES>());
-        tma_load_3d(sin0 + (uint32_t)(q % NI) * SLOT, tmap, bx0, ys - R, slot, bar);
+        tma_load_3d(sin0 + (uint32_t)g * SLOT, tmap, bx0, ys - R, slot, bar);
     }
 
     // zero-copy input: plane z comes from the mapped host grid
@@ -153,7 +161,7 @@ struct StarTB {
         constexpr int VEC = 16 / ES, NV = LXB / VEC;
         const int z = za + q;
         const T* base = hin + (int64_t)z * plane;
-        T* sb = const_cast<T*>(sin) + (q % NI) * (SLOT / ES);
+        T* sb = const_cast<T*>(sin) + ((gb + q) % NI) * (SLOT / ES);
         for (int v = threadIdx.x; v < ROWS * NV; v += S::NT) {
             const int row = v / NV, cv = v - row * NV;
             const int gy = ys - R + row, gx = bx0 + cv * VEC;
@@ -170,7 +178,7 @@ struct StarTB {
         const int z = za + p;
         const int slot = (int)((a.in_slot0 + (int64_t)(z - (int)a.in_lo)) % a.in_cap);
         T* dst = const_cast<T*>(static_cast<const T*>(a.in)) + (int64_t)slot * plane;
-        const T* sb = sin + (p % NI) * (SLOT / ES);
+        const T* sb = sin + ((gb + p) % NI) * (SLOT / ES);
         const int x0 = xs + S::HXA, y0 = ys + S::HY;
         for (int v = threadIdx.x; v < S::TY * NV; v += S::NT) {
             const int r = v / NV, cv = v - r * NV;
@@ -305,7 +313,7 @@ struct StarTB {
         float2 v[VY][2], done[VY][2];
         constexpr int PHL = pmod(PH - L * (R + 1), W2);
         if constexpr (L == 0) {
-            const T* rows = sin + (p % NI) * (SLOT / ES);
+            const T* rows = sin + ((gb + p) % NI) * (SLOT / ES);
 #pragma unroll
             for (int y = 0; y < VY; ++y) {
                 const float4 q = lds4(rows + (my_row + y + R) * LXB + col0);
@@ -392,15 +400,18 @@ struct StarTB {
     template <int PH>
     __device__ __forceinline__ bool phase(int p0) {
         const int p = p0 + PH;
+        const int g = (gb + p) % NI;
         bool late = false;
         bool hp = false;
         if constexpr (ZC) hp = host_plane(za + p);
+        const bool tma = !hp && za + p < zb;
         if (hp) cp_async_wait_group<PD - 1>();  // one group per phase: this phase's has landed
-        else if (za + p < zb) late = !mbar_wait_bounded(bar0 + (uint32_t)(p % NI) * 8u, (uint32_t)((p / NI) & 1));
+        else if (tma) late = !mbar_wait_bounded(bar0 + (uint32_t)g * 8u, (par >> g) & 1u);
         if (__syncthreads_or(late)) {
             pfail = p;
             return false;
         }
+        if (tma) par ^= 1u << g;  // (flipped only once every thread saw the copy land)
         // the slot of phase p + PD last held phase p - 1, read before the barrier
         if constexpr (ZC) {
             if (hp) write_back(p);
@@ -419,29 +430,16 @@ struct StarTB {
         return true;
     }
 
-    __device__ __forceinline__ void run(unsigned char* smem) {
-        bar0 = smem_u32(smem);
-        sin = reinterpret_cast<const T*>(smem + S::kBarBytes);
-        sin0 = bar0 + S::kBarBytes;
-        slev = reinterpret_cast<float*>(smem + S::kBarBytes + NI * SLOT);
-        lane = threadIdx.x & 31;
-        warp = threadIdx.x >> 5;
-        my_row = warp * VY;
-        const int x0 = (int)blockIdx.x * S::TX, y0 = (int)blockIdx.y * S::TY;
+    // one piece: output planes [zs, ze) of tile (tx, ty); false when an input
+    // copy did not land in time
+    __device__ __forceinline__ bool piece(int tx, int ty, int zs, int ze) {
+        const int x0 = tx * S::TX, y0 = ty * S::TY;
         xs = x0 - S::HXA;
         ys = y0 - S::HY;
-        ny = (int)a.ny;
-        nx = (int)a.nx;
-        plane = a.ny * a.nx;
-        n0 = (int)a.n0;
         gx0 = xs + lane * 4;
         xin = gx0 >= 0 && gx0 < nx;  // nx % 4 == 0: a vector is all in or all out
         bx0 = ES == 4 ? xs : (xs & ~7);  // 16-byte aligned box start
         col0 = (xs - bx0) + lane * 4;
-        out = static_cast<T*>(a.out);
-        hin = static_cast<const T*>(a.host_in);
-        hlo = ZC && hin ? (int)a.host_lo : 0;
-        hhi = ZC && hin ? (int)a.host_hi : 0;
         inyx = 0;
 #pragma unroll
         for (int y = 0; y < VY; ++y)
@@ -478,11 +476,8 @@ struct StarTB {
             for (int y = 0; y < VY; ++y)
 #pragma unroll
                 for (int h = 0; h < 2; ++h) C[l][y][h] = make_float2(0.f, 0.f);
-        // axis-0 segment of this CTA: outputs [zs, ze), stream over [za, zb)
-        const int nseg = gridDim.z;
-        const int nout = (int)(a.out_hi - a.out_lo), in_lo = (int)a.in_lo, in_hi = (int)a.in_hi;
-        const int zs = (int)a.out_lo + (int)((int64_t)nout * blockIdx.z / nseg);
-        const int ze = (int)a.out_lo + (int)((int64_t)nout * (blockIdx.z + 1) / nseg);
+        // stream over [za, zb): the outputs and the K*R planes each side
+        const int in_lo = (int)a.in_lo, in_hi = (int)a.in_hi;
         za = zs - K * R > in_lo ? zs - K * R : in_lo;
         zb = ze + K * R < in_hi ? ze + K * R : in_hi;
         olo = need_lo = zs;
@@ -500,12 +495,9 @@ struct StarTB {
         // last arrival any level needs: level K-1 at plane need_hi + R - 1
         const int nph0 = (need_hi + R - 1 - za) + (K - 1) * (R + 1) + 1;
         const int nph = (nph0 + W2 - 1) / W2 * W2;
-        if (threadIdx.x == 0) {
-#pragma unroll
-            for (int i = 0; i < NI; ++i) mbar_init(bar0 + 8u * i, 1);
-            fence_mbar_init();
-        }
-        __syncthreads();
+        // (the slots were last read through the generic proxy by the previous
+        // piece, behind the barrier that ended it)
+        if (threadIdx.x == 0) fence_proxy_async_smem();
         for (int q = 0; q < PD; ++q) {
             if constexpr (ZC) {
                 if (host_plane(za + q)) stage_host(q);
@@ -517,15 +509,90 @@ struct StarTB {
         }
         bool ok = true;
         for (int p0 = 0; p0 < nph && ok; p0 += W2) ok = phase<0>(p0);
+        return ok;
+    }
+
+    __device__ __forceinline__ void run(unsigned char* smem) {
+        bar0 = smem_u32(smem);
+        sin = reinterpret_cast<const T*>(smem + S::kBarBytes);
+        sin0 = bar0 + S::kBarBytes;
+        slev = reinterpret_cast<float*>(smem + S::kBarBytes + NI * SLOT);
+        lane = threadIdx.x & 31;
+        warp = threadIdx.x >> 5;
+        my_row = warp * VY;
+        ny = (int)a.ny;
+        nx = (int)a.nx;
+        plane = a.ny * a.nx;
+        n0 = (int)a.n0;
+        out = static_cast<T*>(a.out);
+        hin = static_cast<const T*>(a.host_in);
+        hlo = ZC && hin ? (int)a.host_lo : 0;
+        hhi = ZC && hin ? (int)a.host_hi : 0;
+        gb = 0;
+        par = 0;
+        if (threadIdx.x == 0) {
+#pragma unroll
+            for (int i = 0; i < NI; ++i) mbar_init(bar0 + 8u * i, 1);
+            fence_mbar_init();
+        }
+        __syncthreads();
+        // this CTA's pieces.  Grid split: one tile and axis-0 segment.  Round
+        // split (a.split = n segments per tile): the tiles x n units, segment-
+        // major as the grid split orders them, go to the G CTAs in rounds
+        // (unit c + iG in round i), and the U mod G units of the last,
+        // partial round are each cut into floor(G / (U mod G)) pieces along
+        // axis 0, so that every CTA ends at about the same time; neighbouring
+        // CTAs work on neighbouring tiles at the same planes throughout
+        const int64_t nout = a.out_hi - a.out_lo;
+        const int tiles_x = (nx + S::TX - 1) / S::TX;
+        const int64_t tiles = (int64_t)tiles_x * ((ny + S::TY - 1) / S::TY);
+        const int nseg = a.split ? a.split : (int)gridDim.z;
+        const int64_t G = gridDim.x, units = tiles * nseg;
+        const int64_t F = a.split ? units / G : 1;  // whole-unit rounds
+        const int64_t rem = a.split ? units - F * G : 0;
+        const int64_t jr = rem ? G / rem : 1;        // pieces per unit of the last round
+        const int64_t c = blockIdx.x;
+        bool ok = true, ran = false;
+        for (int64_t i = 0; i <= F; ++i) {
+            int64_t v, k = 0, nk = 1;
+            if (!a.split) {
+                v = blockIdx.x + (int64_t)blockIdx.y * tiles_x + (int64_t)blockIdx.z * tiles;
+                if (i == F) break;
+            } else if (i < F) {
+                v = c + i * G;
+            } else {
+                if (c >= jr * rem) break;
+                v = F * G + c % rem;
+                k = c / rem;
+                nk = jr;
+            }
+            const int64_t t = v % tiles, sg = v / tiles;
+            const int64_t s0 = nout * sg / nseg, s1 = nout * (sg + 1) / nseg;
+            const int zs = (int)(a.out_lo + s0 + (s1 - s0) * k / nk);
+            const int ze = (int)(a.out_lo + s0 + (s1 - s0) * (k + 1) / nk);
+            if (ze <= zs) continue;
+            if (ran) {
+                // the next piece reuses the staging slots and level planes
+                gb += zb - za;
+                __syncthreads();
+            }
+            ok = piece((int)(t % tiles_x), (int)(t / tiles_x), zs, ze);
+            ran = true;
+            if (!ok) break;
+        }
         if (!ok) {
             // a copy did not land: report it and wait (bounded) for the
             // copies still in flight before the shared memory is released
             if (threadIdx.x == 0) {
                 if (a.status) atomicOr(a.status, 1);
                 // phases pfail .. pfail + PD - 1 were issued and not consumed
-                for (int q = pfail; q < pfail + PD && za + q < zb; ++q)
-                    if (!ZC || !host_plane(za + q))
-                        (void)mbar_wait_bounded(bar0 + (uint32_t)(q % NI) * 8u, (uint32_t)((q / NI) & 1));
+                unsigned pq = par;
+                for (int q = pfail; q < pfail + PD && za + q < zb; ++q) {
+                    if (ZC && host_plane(za + q)) continue;
+                    const int g = (gb + q) % NI;
+                    (void)mbar_wait_bounded(bar0 + (uint32_t)g * 8u, (pq >> g) & 1u);
+                    pq ^= 1u << g;
+                }
             }
             __syncthreads();
         }

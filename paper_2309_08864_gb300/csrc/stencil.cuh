@@ -50,6 +50,10 @@ struct StencilArgs {
     // launches that read them later
     const void* host_in;
     int64_t host_lo, host_hi;
+    // 3D star kernel work split: 0 = one tile and axis-0 segment per CTA
+    // (grid: tiles in x, tiles in y, segments); 1 = the launch's tiles x
+    // output planes cut into gridDim.x equal contiguous ranges, tile-major
+    int split;
 };
 
 template <typename T> struct Compute { using type = float; };

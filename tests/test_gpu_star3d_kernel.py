@@ -44,3 +44,34 @@ def test_star3d_16bit_out_of_core(dtype, kon, koff, T):
     """16-bit storage through the out-of-core pipeline: equal to the in-core
     run byte for byte, and within the format's rounding of the oracle."""
     check_case((57, 46, 136), 1, "star", [0.4] + [0.1] * 6, T, dtype, 4, kon, koff, 0)
+
+
+@pytest.mark.parametrize("split", ["grid", "rounds"])
+@pytest.mark.parametrize("dims", [(41, 70, 264), (150, 96, 512)])
+@pytest.mark.parametrize("r,kon", CASES)
+def test_star3d_work_splits_match_generic_kernel_bitwise(r, kon, dims, split, monkeypatch):
+    """Both work splits of a launch -- one tile and axis-0 segment per CTA, or
+    the (tile, output plane) pairs cut into one contiguous range per CTA, whose
+    pieces start and end inside tiles -- give the generic kernel's bytes."""
+    import torch
+    T = kon + 1
+    dtype = so2dr.F32 if r != 2 else so2dr.BF16
+    st = inputs.to_storage(inputs.draw_box(5, dims), dtype)
+    c = _coeffs(3, r, "star")
+    plan = so2dr.Plan(dims, r, "star", c, T, k_on=kon, k_off=T, budget_bytes=0, dtype=dtype)
+    monkeypatch.setenv("SO2DR_WORK_SPLIT", split)
+    fast = gu.pinned_from_storage(st.copy(), dtype)
+    plan.run(fast, in_core=True)
+    monkeypatch.setenv("SO2DR_GENERIC_KERNEL", "1")
+    generic = gu.pinned_from_storage(st.copy(), dtype)
+    plan.run(generic, in_core=True)
+    plan.close()
+    assert torch.equal(fast.view(torch.uint8), generic.view(torch.uint8))
+
+
+@pytest.mark.parametrize("split", ["grid", "rounds"])
+def test_star3d_work_splits_out_of_core(split, monkeypatch):
+    """The out-of-core pipeline under either work split equals the in-core
+    run byte for byte (trapezoid launches of every size, ragged chunks)."""
+    monkeypatch.setenv("SO2DR_WORK_SPLIT", split)
+    check_case((97, 70, 264), 1, "star", [0.4] + [0.1] * 6, 13, so2dr.F32, 5, 4, 8, 0)
