@@ -186,10 +186,10 @@ void choose_work_split(LaunchShape& ls, int64_t nout, int r, int depth, int sms,
         if (best_n == 0 || cost < best * 0.98) { best_n = n; best = cost; }
     }
     const char* pin = std::getenv("SO2DR_WORK_SPLIT");
-    // (measured on GB300: the round split gains 4% on depth-4 launches and
-    // loses up to 9% on depth-2 ones, where the model rated it 7% better, so
-    // it is taken for fused depths of 3 and more only)
-    bool rounds = depth >= 3 && best < cost_grid * 0.97;
+    // (measured on GB300: the round split gains 3-5% on radius-1 depth-4
+    // launches, in-core and out-of-core, and loses 9-13% at depths 2 and 3,
+    // where the model rated it 4-7% better, so only depth 4 takes it)
+    bool rounds = depth >= 4 && best < cost_grid * 0.97;
     if (pin && std::strcmp(pin, "grid") == 0) rounds = false;
     if (pin && std::strcmp(pin, "rounds") == 0) rounds = true;
     if (rounds) {

@@ -62,7 +62,7 @@ int choose_segments(int64_t tiles, int64_t nout, int r, int depth, int sms, int 
 // cut into shorter axis-0 pieces (*split = n), whichever the cost model
 // (busiest SM's CTAs times planes streamed, each piece paying the r * depth
 // halo each side and the depth-deep pipeline fill) rates cheaper by 3%, for
-// fused depths of 3 and more.  SO2DR_WORK_SPLIT=grid|rounds pins the choice.
+// fused depths of 4 and more.  SO2DR_WORK_SPLIT=grid|rounds pins the choice.
 void choose_work_split(LaunchShape& ls, int64_t nout, int r, int depth, int sms, int occ, int* split);
 
 // Per-dtype instantiations (one translation unit each).

@@ -99,6 +99,8 @@ struct StarTB {
                          PD = S::PD, NB = S::NB, W2 = 2 * R, ES = (int)sizeof(T), LXB = S::template lxb<ES>(),
                          SLOT = S::template in_slot_bytes<ES>();
     static constexpr unsigned kAll = (1u << (4 * VY)) - 1u;
+    static constexpr int kWorkOff = 64;  // work-split constants, behind the mbarriers
+    static_assert(NI * 8 <= kWorkOff && kWorkOff + 6 * 4 <= S::kBarBytes, "barrier block layout");
 
     const StencilArgs& a;
     const CUtensorMap* tmap;
@@ -530,53 +532,62 @@ struct StarTB {
         hhi = ZC && hin ? (int)a.host_hi : 0;
         gb = 0;
         par = 0;
-        if (threadIdx.x == 0) {
-#pragma unroll
-            for (int i = 0; i < NI; ++i) mbar_init(bar0 + 8u * i, 1);
-            fence_mbar_init();
-        }
-        __syncthreads();
         // this CTA's pieces.  Grid split: one tile and axis-0 segment.  Round
         // split (a.split = n segments per tile): the tiles x n units, segment-
         // major as the grid split orders them, go to the G CTAs in rounds
         // (unit c + iG in round i), and the U mod G units of the last,
         // partial round are each cut into floor(G / (U mod G)) pieces along
         // axis 0, so that every CTA ends at about the same time; neighbouring
-        // CTAs work on neighbouring tiles at the same planes throughout
-        const int64_t nout = a.out_hi - a.out_lo;
-        const int tiles_x = (nx + S::TX - 1) / S::TX;
-        const int64_t tiles = (int64_t)tiles_x * ((ny + S::TY - 1) / S::TY);
-        const int nseg = a.split ? a.split : (int)gridDim.z;
-        const int64_t G = gridDim.x, units = tiles * nseg;
-        const int64_t F = a.split ? units / G : 1;  // whole-unit rounds
-        const int64_t rem = a.split ? units - F * G : 0;
-        const int64_t jr = rem ? G / rem : 1;        // pieces per unit of the last round
-        const int64_t c = blockIdx.x;
+        // CTAs work on neighbouring tiles at the same planes throughout.  The
+        // constants of the enumeration sit in shared memory (behind the
+        // mbarriers) and are read again for every piece, so that they hold
+        // no registers while a piece streams.
+        volatile int* wk = reinterpret_cast<volatile int*>(smem + kWorkOff);
+        if (threadIdx.x == 0) {
+#pragma unroll
+            for (int i = 0; i < NI; ++i) mbar_init(bar0 + 8u * i, 1);
+            fence_mbar_init();
+            const int tiles_x = (nx + S::TX - 1) / S::TX;
+            const int tiles = tiles_x * ((ny + S::TY - 1) / S::TY);
+            const int nseg = a.split ? a.split : (int)gridDim.z;
+            const int G = (int)gridDim.x, units = tiles * nseg;
+            const int F = a.split ? units / G : 1;  // whole-unit rounds
+            const int rem = a.split ? units - F * G : 0;
+            wk[0] = F;
+            wk[1] = rem;
+            wk[2] = rem ? G / rem : 1;  // pieces per unit of the last round
+            wk[3] = tiles_x;
+            wk[4] = tiles;
+            wk[5] = nseg;
+        }
+        __syncthreads();
         bool ok = true, ran = false;
-        for (int64_t i = 0; i <= F; ++i) {
-            int64_t v, k = 0, nk = 1;
+        for (int i = 0; i <= wk[0]; ++i) {
+            const int F = wk[0], rem = wk[1], jr = wk[2], tiles_x = wk[3], tiles = wk[4], nseg = wk[5];
+            int v, k = 0, nk = 1;
             if (!a.split) {
-                v = blockIdx.x + (int64_t)blockIdx.y * tiles_x + (int64_t)blockIdx.z * tiles;
                 if (i == F) break;
+                v = (int)blockIdx.x + (int)blockIdx.y * tiles_x + (int)blockIdx.z * tiles;
             } else if (i < F) {
-                v = c + i * G;
+                v = (int)blockIdx.x + i * (int)gridDim.x;
             } else {
-                if (c >= jr * rem) break;
-                v = F * G + c % rem;
-                k = c / rem;
+                if ((int)blockIdx.x >= jr * rem) break;
+                v = F * (int)gridDim.x + (int)blockIdx.x % rem;
+                k = (int)blockIdx.x / rem;
                 nk = jr;
             }
-            const int64_t t = v % tiles, sg = v / tiles;
-            const int64_t s0 = nout * sg / nseg, s1 = nout * (sg + 1) / nseg;
-            const int zs = (int)(a.out_lo + s0 + (s1 - s0) * k / nk);
-            const int ze = (int)(a.out_lo + s0 + (s1 - s0) * (k + 1) / nk);
+            const int t = v % tiles, sg = v / tiles;
+            const int64_t nout = a.out_hi - a.out_lo;
+            const int s0 = (int)(nout * sg / nseg), s1 = (int)(nout * (sg + 1) / nseg);
+            const int zs = (int)a.out_lo + s0 + (int)((int64_t)(s1 - s0) * k / nk);
+            const int ze = (int)a.out_lo + s0 + (int)((int64_t)(s1 - s0) * (k + 1) / nk);
             if (ze <= zs) continue;
             if (ran) {
                 // the next piece reuses the staging slots and level planes
                 gb += zb - za;
                 __syncthreads();
             }
-            ok = piece((int)(t % tiles_x), (int)(t / tiles_x), zs, ze);
+            ok = piece(t % tiles_x, t / tiles_x, zs, ze);
             ran = true;
             if (!ok) break;
         }
