@@ -423,7 +423,13 @@ def run_kernel_case(args):
         dims, kind, coeffs = (n, n), "box", list(inputs.box2d_coeffs(r))
     else:
         dims, kind = (n, n, n), "star"
-        coeffs = [0.4] + [0.1] * 6 if r == 1 else list(inputs.radius4_star_coeffs())
+        if r == 1:
+            coeffs = [0.4] + [0.1] * 6
+        elif r == 4:
+            coeffs = list(inputs.radius4_star_coeffs())
+        else:  # 6r + 1 seeded weights summing to 1, as for radius 4
+            c = inputs.draw_box(7, (6 * r + 1,), dist="uniform", a=0.5, b=1.5)
+            coeffs = list(c / c.sum())
     cells = 1
     for e in dims:
         cells *= e

@@ -178,6 +178,12 @@ typedef struct {
  *                         the driver and run slower).
  *   SO2DR_ADJOINT_STEPS=K backward steps per adjoint round (or the largest
  *                         K below it that fits the arena; default: chosen).
+ *   SO2DR_WORK_SPLIT      how a 3D star launch spreads over the SMs (default:
+ *                         chosen per launch): grid = one tile and axis-0
+ *                         segment per CTA; rounds = one CTA per SM slot
+ *                         taking (tile, segment) units in rounds; waves = the
+ *                         grid split with segments counted in waves of
+ *                         resident CTAs.  Results are the same bytes.
  * A kernel whose bounded wait for a staged plane gives up (after about two
  * seconds) sets the run list's device status word; so2dr_run then returns
  * SO2DR_E_TIMEOUT.

@@ -148,18 +148,20 @@ int stencil_occupancy(int dtype, int shape, int r, int depth, const LaunchShape&
     }
 }
 
-int choose_segments(int64_t tiles, int64_t nout, int r, int depth, int sms, int occ) {
+int choose_segments(int64_t tiles, int64_t nout, int r, int depth, int sms, int occ, bool share_sm) {
     if (tiles <= 0 || nout <= 0 || sms <= 0) return 1;
-    (void)occ;
+    const int64_t slots = (int64_t)sms * (share_sm || occ < 1 ? 1 : occ);
     int best = 1;
     double best_cost = 0;
     for (int n = 1; n <= 64 && n <= nout; ++n) {
-        // the CTAs resident on one SM share its throughput, so an SM's time
-        // goes with the CTAs it receives (the busiest SM gets
-        // ceil(tiles * n / sms)) times the planes each streams
-        int64_t per_sm = (tiles * n + sms - 1) / sms;
+        // share_sm: the CTAs resident on one SM share its throughput, so an
+        // SM's time goes with the CTAs it receives (the busiest SM gets
+        // ceil(tiles * n / sms)) times the planes each streams; otherwise the
+        // occ resident CTAs of an SM run side by side, and the time goes with
+        // the waves of sms * occ CTAs
+        int64_t per_slot = (tiles * n + slots - 1) / slots;
         double len = (double)nout / n + 2.0 * r * depth + depth;
-        double cost = (double)per_sm * len;
+        double cost = (double)per_slot * len;
         if (n == 1 || cost < best_cost * 0.98) { best = n; best_cost = cost; }
     }
     return best;
@@ -169,7 +171,11 @@ void choose_work_split(LaunchShape& ls, int64_t nout, int r, int depth, int sms,
     *split = 0;
     const int64_t tiles = (int64_t)ls.grid.x * ls.grid.y;
     if (tiles <= 0 || nout <= 0 || sms <= 0) return;
-    const int nseg = choose_segments(tiles, nout, r, depth, sms, occ);
+    const char* pin = std::getenv("SO2DR_WORK_SPLIT");
+    // grid split: segments by the shared-SM model, or by waves of resident
+    // CTAs (SO2DR_WORK_SPLIT=waves)
+    const bool waves = pin && std::strcmp(pin, "waves") == 0;
+    const int nseg = choose_segments(tiles, nout, r, depth, sms, occ, !waves);
     const double ovh = 2.0 * r * depth + depth;
     const double cost_grid = (double)((tiles * nseg + sms - 1) / sms) * ((double)nout / nseg + ovh);
     // round split: G = sms * occ CTAs take the tiles x n units in rounds;
@@ -185,12 +191,11 @@ void choose_work_split(LaunchShape& ls, int64_t nout, int r, int depth, int sms,
         cost *= (double)occ1;
         if (best_n == 0 || cost < best * 0.98) { best_n = n; best = cost; }
     }
-    const char* pin = std::getenv("SO2DR_WORK_SPLIT");
     // (measured on GB300: the round split gains 3-5% on radius-1 depth-4
     // launches, in-core and out-of-core, and loses 9-13% at depths 2 and 3,
     // where the model rated it 4-7% better, so only depth 4 takes it)
     bool rounds = depth >= 4 && best < cost_grid * 0.97;
-    if (pin && std::strcmp(pin, "grid") == 0) rounds = false;
+    if (pin && (std::strcmp(pin, "grid") == 0 || waves)) rounds = false;
     if (pin && std::strcmp(pin, "rounds") == 0) rounds = true;
     if (rounds) {
         ls.grid = dim3((unsigned)G, 1, 1);

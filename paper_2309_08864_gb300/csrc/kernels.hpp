@@ -50,10 +50,13 @@ cudaError_t launch_stencil(int dtype, int shape, int r, const StencilArgs& a, co
 int stencil_occupancy(int dtype, int shape, int r, int depth, const LaunchShape& ls);
 
 // Axis-0 segments for a launch with `tiles` CTAs per segment, nout output
-// planes and halo r*depth: the count that minimises the CTAs the busiest SM
-// receives times the planes each streams (occ: CTAs per SM, unused: resident
-// CTAs share the SM's throughput).
-int choose_segments(int64_t tiles, int64_t nout, int r, int depth, int sms, int occ);
+// planes and halo r*depth: the count that minimises the busiest SM's time.
+// share_sm: the occ resident CTAs of an SM share its throughput, so the time
+// goes with the CTAs the busiest SM receives times the planes each streams
+// (the 3D star kernel, issue-bound); otherwise they run side by side and the
+// time goes with the waves of sms * occ CTAs (the 2D box kernel, whose second
+// resident CTA hides the first one's latency).
+int choose_segments(int64_t tiles, int64_t nout, int r, int depth, int sms, int occ, bool share_sm);
 
 // Work split of a 3D star kernel launch (ls.grid is tiles in x by tiles in
 // y): either axis-0 segments per tile, one CTA each (choose_segments; *split
@@ -62,7 +65,8 @@ int choose_segments(int64_t tiles, int64_t nout, int r, int depth, int sms, int 
 // cut into shorter axis-0 pieces (*split = n), whichever the cost model
 // (busiest SM's CTAs times planes streamed, each piece paying the r * depth
 // halo each side and the depth-deep pipeline fill) rates cheaper by 3%, for
-// fused depths of 4 and more.  SO2DR_WORK_SPLIT=grid|rounds pins the choice.
+// fused depths of 4 and more.  SO2DR_WORK_SPLIT=grid|rounds pins the choice
+// (waves: the grid split with segments counted in waves of resident CTAs).
 void choose_work_split(LaunchShape& ls, int64_t nout, int r, int depth, int sms, int occ, int* split);
 
 // Per-dtype instantiations (one translation unit each).

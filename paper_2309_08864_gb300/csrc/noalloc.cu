@@ -162,7 +162,7 @@ extern "C" int so2dr_run_device_noalloc(int ndim, const int64_t* dims, int radiu
         if (ls.fast) {
             int occ = stencil_occupancy(dtype, shape, radius, depth, ls);
             if (ls.fast == kFastStar3D) choose_work_split(ls, n0, radius, depth, sms, occ, &a.split);
-            else ls.grid.z = (unsigned)choose_segments((int64_t)ls.grid.x * ls.grid.y, n0, radius, depth, sms, occ);
+            else ls.grid.z = (unsigned)choose_segments((int64_t)ls.grid.x * ls.grid.y, n0, radius, depth, sms, occ, false);
         }
         a.in = src;
         a.in_cap = n0;

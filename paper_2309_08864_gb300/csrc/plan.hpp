@@ -188,6 +188,10 @@ size_t adjoint_arena_bytes(const Plan& q);
 // ------------------------------------------------------------- op helpers
 
 constexpr int64_t kAlign = 256;
+// the last kAlign bytes of a run list's arena: the device status word at 0,
+// the round split's piece counters of the streams (two words each) from here
+constexpr int64_t kWorkCtrOff = 16;
+static_assert(kWorkCtrOff + 8 * kNumStreams <= kAlign, "status block layout");
 inline int64_t align_up(int64_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 inline int64_t floor_mod(int64_t a, int64_t m) { return ((a % m) + m) % m; }
 

@@ -225,9 +225,14 @@ int enqueue_stencil(so2dr_plan_s* P, const RunList& rl, const Op& op, cudaStream
         if (!occ) occ = stencil_occupancy(p.dtype, shape, p.r, o.depth, ls);
         if (ls.fast == kFastStar3D) {
             choose_work_split(ls, o.dst_hi - o.dst_lo, p.r, o.depth, P->sm_count, occ, &a.split);
+            // the round split's piece counter: one per stream (the launches
+            // of a stream run one after another), beside the status word
+            if (a.split && o.stream >= 0 && o.stream < kNumStreams)
+                a.work_ctr = reinterpret_cast<unsigned*>(P->arena + rl.arena_bytes - kAlign + kWorkCtrOff +
+                                                         8 * o.stream);
         } else {
             int64_t tiles = (int64_t)ls.grid.x * ls.grid.y;
-            ls.grid.z = (unsigned)choose_segments(tiles, o.dst_hi - o.dst_lo, p.r, o.depth, P->sm_count, occ);
+            ls.grid.z = (unsigned)choose_segments(tiles, o.dst_hi - o.dst_lo, p.r, o.depth, P->sm_count, occ, false);
         }
     }
     cudaError_t e = launch_stencil(p.dtype, shape, p.r, a, ls, s);
@@ -252,8 +257,9 @@ int execute(so2dr_plan_s* P, const RunList& rl, char* const* hosts, const int64_
     cudaStream_t* st = P->st;
     // device status word (the last kAlign bytes of the run list's arena): a
     // kernel whose bounded wait for a copy gave up sets it
+    // (and, after it, the round split's piece counters of the streams)
     int* status = reinterpret_cast<int*>(P->arena + rl.arena_bytes - kAlign);
-    if ((e = cudaMemsetAsync(status, 0, sizeof(int), st[kStreamH2D])) != cudaSuccess)
+    if ((e = cudaMemsetAsync(status, 0, kWorkCtrOff + 8 * kNumStreams, st[kStreamH2D])) != cudaSuccess)
         return cuda_fail(e, "cudaMemsetAsync(status)");
     // start marker: the compute and D2H streams start after everything the
     // caller queued on the H2D stream

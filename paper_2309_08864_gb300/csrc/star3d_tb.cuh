@@ -100,7 +100,7 @@ struct StarTB {
                          SLOT = S::template in_slot_bytes<ES>();
     static constexpr unsigned kAll = (1u << (4 * VY)) - 1u;
     static constexpr int kWorkOff = 64;  // work-split constants, behind the mbarriers
-    static_assert(NI * 8 <= kWorkOff && kWorkOff + 6 * 4 <= S::kBarBytes, "barrier block layout");
+    static_assert(NI * 8 <= kWorkOff && kWorkOff + 8 * 4 <= S::kBarBytes, "barrier block layout");
 
     const StencilArgs& a;
     const CUtensorMap* tmap;
@@ -534,14 +534,17 @@ struct StarTB {
         par = 0;
         // this CTA's pieces.  Grid split: one tile and axis-0 segment.  Round
         // split (a.split = n segments per tile): the tiles x n units, segment-
-        // major as the grid split orders them, go to the G CTAs in rounds
-        // (unit c + iG in round i), and the U mod G units of the last,
-        // partial round are each cut into floor(G / (U mod G)) pieces along
-        // axis 0, so that every CTA ends at about the same time; neighbouring
-        // CTAs work on neighbouring tiles at the same planes throughout.  The
-        // constants of the enumeration sit in shared memory (behind the
-        // mbarriers) and are read again for every piece, so that they hold
-        // no registers while a piece streams.
+        // major as the grid split orders them, are pieces 0 .. FG-1 (F whole
+        // rounds of the G CTAs), and the U mod G units of the last, partial
+        // round are each cut into floor(G / (U mod G)) pieces along axis 0
+        // (pieces FG.., cut-major, so that pieces taken at the same time are
+        // neighbouring tiles at the same planes).  The CTAs take the pieces
+        // in order from the launch's counter (a.work_ctr), so that an SM that
+        // finished a cheap piece takes the next one; without a counter CTA c
+        // takes pieces c, c + G, c + 2G, ...  The constants of the
+        // enumeration sit in shared memory (behind the mbarriers) and are
+        // read again for every piece, so that they hold no registers while a
+        // piece streams.
         volatile int* wk = reinterpret_cast<volatile int*>(smem + kWorkOff);
         if (threadIdx.x == 0) {
 #pragma unroll
@@ -553,29 +556,44 @@ struct StarTB {
             const int G = (int)gridDim.x, units = tiles * nseg;
             const int F = a.split ? units / G : 1;  // whole-unit rounds
             const int rem = a.split ? units - F * G : 0;
-            wk[0] = F;
+            const int jr = rem ? G / rem : 1;        // pieces per unit of the last round
+            wk[0] = F * G;
             wk[1] = rem;
-            wk[2] = rem ? G / rem : 1;  // pieces per unit of the last round
+            wk[2] = jr;
             wk[3] = tiles_x;
             wk[4] = tiles;
             wk[5] = nseg;
+            wk[6] = F * G + jr * rem;                 // pieces
         }
         __syncthreads();
         bool ok = true, ran = false;
-        for (int i = 0; i <= wk[0]; ++i) {
-            const int F = wk[0], rem = wk[1], jr = wk[2], tiles_x = wk[3], tiles = wk[4], nseg = wk[5];
+        for (int i = 0;; ++i) {
             int v, k = 0, nk = 1;
             if (!a.split) {
-                if (i == F) break;
-                v = (int)blockIdx.x + (int)blockIdx.y * tiles_x + (int)blockIdx.z * tiles;
-            } else if (i < F) {
-                v = (int)blockIdx.x + i * (int)gridDim.x;
+                if (i > 0) break;
+                v = (int)blockIdx.x + (int)blockIdx.y * wk[3] + (int)blockIdx.z * wk[4];
             } else {
-                if ((int)blockIdx.x >= jr * rem) break;
-                v = F * (int)gridDim.x + (int)blockIdx.x % rem;
-                k = (int)blockIdx.x / rem;
-                nk = jr;
+                int u;
+                if (a.work_ctr) {
+                    if (threadIdx.x == 0) wk[7] = (int)atomicAdd(a.work_ctr, 1u);
+                    __syncthreads();
+                    u = wk[7];
+                    __syncthreads();
+                } else {
+                    u = (int)blockIdx.x + i * (int)gridDim.x;
+                }
+                if (u >= wk[6]) break;
+                const int FG = wk[0];
+                if (u < FG) {
+                    v = u;
+                } else {
+                    const int w = u - FG, rem = wk[1];
+                    k = w / rem;
+                    v = FG + w % rem;
+                    nk = wk[2];
+                }
             }
+            const int tiles_x = wk[3], tiles = wk[4], nseg = wk[5];
             const int t = v % tiles, sg = v / tiles;
             const int64_t nout = a.out_hi - a.out_lo;
             const int s0 = (int)(nout * sg / nseg), s1 = (int)(nout * (sg + 1) / nseg);
@@ -608,6 +626,16 @@ struct StarTB {
             __syncthreads();
         }
         if constexpr (ZC) cp_async_wait_all();  // no cp.async copy outlives the CTA
+        if (a.split && a.work_ctr && threadIdx.x == 0) {
+            // the last CTA to finish (every other one has taken its last
+            // piece) zeroes the counter for the next launch on this stream
+            __threadfence();
+            if (atomicAdd(a.work_ctr + 1, 1u) == gridDim.x - 1) {
+                a.work_ctr[0] = 0u;
+                a.work_ctr[1] = 0u;
+                __threadfence();
+            }
+        }
     }
 };
 

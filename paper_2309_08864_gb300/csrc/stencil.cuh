@@ -51,9 +51,14 @@ struct StencilArgs {
     const void* host_in;
     int64_t host_lo, host_hi;
     // 3D star kernel work split: 0 = one tile and axis-0 segment per CTA
-    // (grid: tiles in x, tiles in y, segments); 1 = the launch's tiles x
-    // output planes cut into gridDim.x equal contiguous ranges, tile-major
+    // (grid: tiles in x, tiles in y, segments); n > 0 = gridDim.x CTAs take
+    // the tiles x n (tile, segment) units in rounds (the last round's units
+    // cut shorter along axis 0)
     int split;
+    // round split: {next piece, finished CTAs}, zero at launch; the CTAs take
+    // pieces in order from this counter (null: CTA c takes pieces c, c + G, ...)
+    // and the last CTA to finish zeroes both for the next launch on the stream
+    unsigned* work_ctr;
 };
 
 template <typename T> struct Compute { using type = float; };
