@@ -167,6 +167,11 @@ int choose_segments(int64_t tiles, int64_t nout, int r, int depth, int sms, int 
     return best;
 }
 
+// longest unit of the round split (planes; measured on GB300: units of 1024
+// planes ran 1-5% slower than the grid split at fused depths 1-3, units of
+// 341 planes 5% faster at depth 4)
+constexpr double kMaxUnit = 384;
+
 void choose_work_split(LaunchShape& ls, int64_t nout, int r, int depth, int sms, int occ, int* split) {
     *split = 0;
     const int64_t tiles = (int64_t)ls.grid.x * ls.grid.y;
@@ -186,15 +191,15 @@ void choose_work_split(LaunchShape& ls, int64_t nout, int r, int depth, int sms,
     for (int n = 1; n <= 64 && n <= nout; ++n) {
         const int64_t units = tiles * n, F = units / G, rem = units - F * G;
         const double len = std::ceil((double)nout / n);
+        // units of more than kMaxUnit planes let neighbouring CTAs drift
+        // apart along axis 0, and the halo rows they share then miss in L2
+        if (len > kMaxUnit && n < nout) continue;
         double cost = (double)F * (len + ovh);
         if (rem) cost += std::ceil(len / (double)(G / rem)) + ovh;
         cost *= (double)occ1;
         if (best_n == 0 || cost < best * 0.98) { best_n = n; best = cost; }
     }
-    // (measured on GB300: the round split gains 3-5% on radius-1 depth-4
-    // launches, in-core and out-of-core, and loses 9-13% at depths 2 and 3,
-    // where the model rated it 4-7% better, so only depth 4 takes it)
-    bool rounds = depth >= 4 && best < cost_grid * 0.97;
+    bool rounds = best_n > 0 && best < cost_grid * 0.97;
     if (pin && (std::strcmp(pin, "grid") == 0 || waves)) rounds = false;
     if (pin && std::strcmp(pin, "rounds") == 0) rounds = true;
     if (rounds) {

@@ -64,8 +64,8 @@ int choose_segments(int64_t tiles, int64_t nout, int r, int depth, int sms, int 
 // x n (tile, segment) units in rounds, the units of the last, partial round
 // cut into shorter axis-0 pieces (*split = n), whichever the cost model
 // (busiest SM's CTAs times planes streamed, each piece paying the r * depth
-// halo each side and the depth-deep pipeline fill) rates cheaper by 3%, for
-// fused depths of 4 and more.  SO2DR_WORK_SPLIT=grid|rounds pins the choice
+// halo each side and the depth-deep pipeline fill) rates cheaper by 3%, with
+// units of at most 384 planes.  SO2DR_WORK_SPLIT=grid|rounds pins the choice
 // (waves: the grid split with segments counted in waves of resident CTAs).
 void choose_work_split(LaunchShape& ls, int64_t nout, int r, int depth, int sms, int occ, int* split);
 
