@@ -234,6 +234,12 @@ int enqueue_stencil(so2dr_plan_s* P, const RunList& rl, const Op& op, cudaStream
             int64_t tiles = (int64_t)ls.grid.x * ls.grid.y;
             ls.grid.z = (unsigned)choose_segments(tiles, o.dst_hi - o.dst_lo, p.r, o.depth, P->sm_count, occ, false);
         }
+    } else {
+        // generic kernel: axis-0 segments too, so that a launch of few tiles
+        // (a narrow 2D grid) still spreads over the SMs (one CTA per SM
+        // counted; its shared memory varies with the tile)
+        int64_t tiles = (int64_t)ls.grid.x * ls.grid.y;
+        ls.grid.z = (unsigned)choose_segments(tiles, o.dst_hi - o.dst_lo, p.r, o.depth, P->sm_count, 1, false);
     }
     cudaError_t e = launch_stencil(p.dtype, shape, p.r, a, ls, s);
     if (e != cudaSuccess) return cuda_fail(e, "stencil launch");

@@ -110,12 +110,20 @@ __global__ void __launch_bounds__(256) stencil_tb_kernel(const StencilArgs a) {
 #pragma unroll
     for (int k = 0; k < (int)(sizeof(cst) / sizeof(C)); ++k) cst[k] = (C)a.c[k];
 
-    const int64_t nin = a.in_hi - a.in_lo;
-    const int64_t nsteps = nin + (int64_t)R * a.depth;
+    // axis-0 segment of this CTA (gridDim.z segments): outputs [zs, ze),
+    // streamed over [za, zb), the outputs and the R*depth planes each side
+    // (clipped to the launch's input; a clipped end keeps the launch's own
+    // rule for which planes each level computes)
+    const int64_t nout = a.out_hi - a.out_lo;
+    const int64_t zs = a.out_lo + nout * blockIdx.z / gridDim.z;
+    const int64_t ze = a.out_lo + nout * (blockIdx.z + 1) / gridDim.z;
+    const int64_t za = zs - H > a.in_lo ? zs - H : a.in_lo;
+    const int64_t zb = ze + H < a.in_hi ? ze + H : a.in_hi;
+    const int64_t nsteps = (zb - za) + (int64_t)R * a.depth;
     for (int64_t s = 0; s < nsteps; ++s) {
         // ---- level 0: load input plane z0 into window 0
-        const int64_t z0 = a.in_lo + s;
-        if (z0 < a.in_hi) {
+        const int64_t z0 = za + s;
+        if (z0 < zb) {
             int64_t slot = (a.in_slot0 + (z0 - a.in_lo)) % a.in_cap;
             const T* src = in + slot * plane;
             C* w0 = win + ((z0 - a.in_lo) % W) * tile_cells;
@@ -131,15 +139,15 @@ __global__ void __launch_bounds__(256) stencil_tb_kernel(const StencilArgs a) {
         __syncthreads();
         // ---- fused levels 1..depth
         for (int l = 1; l <= a.depth; ++l) {
-            const int64_t z = a.in_lo + s - (int64_t)l * R;
-            const int64_t lo_l = a.edge_lo ? 0 : a.in_lo + (int64_t)l * R;
-            const int64_t hi_l = a.edge_hi ? a.n0 : a.in_hi - (int64_t)l * R;
+            const int64_t z = za + s - (int64_t)l * R;
+            const int64_t lo_l = za > a.in_lo ? za + (int64_t)l * R : (a.edge_lo ? 0 : a.in_lo + (int64_t)l * R);
+            const int64_t hi_l = zb < a.in_hi ? zb - (int64_t)l * R : (a.edge_hi ? a.n0 : a.in_hi - (int64_t)l * R);
             if (z >= lo_l && z < hi_l) {
                 const C* wp = win + (int64_t)(l - 1) * W * tile_cells;  // level l-1 window
                 const bool zint = z >= R && z < a.n0 - R;
                 const int base = (int)((z - a.in_lo) % W);
                 const bool last = l == a.depth;
-                const bool store_z = last && z >= a.out_lo && z < a.out_hi;
+                const bool store_z = last && z >= zs && z < ze;
                 const int m = l * R;  // level-l in-plane margin inside the loaded tile
                 const int yl0 = (SHAPE == kStar3D || SHAPE == kVarcoef3D) ? m : 0;
                 const int yl1 = (SHAPE == kStar3D || SHAPE == kVarcoef3D) ? ly - m : ly;
