@@ -56,8 +56,8 @@ KERNEL_SRC = {"star": os.path.join(ROOT, "paper_2309_08864_gb300", "csrc", "star
 # bytes per input+output plane times the mean input+output planes of all of
 # the plan's k_on-deep launches (edge chunks clip their trapezoids).
 DRAM_TRAFFIC = {
-    # config: (k_off, k_on of the captured plan, bytes per launch)
-    "0f2c9ddf46dd3e47": {"c2": (22, 4, 441.9e6), "c3": (8, 1, 1558.2e6)},
+    # config: (k_off, k_on of the captured plan, bytes per launch, of which read, written)
+    "0f2c9ddf46dd3e47": {"c2": (22, 4, 441.9e6, 260.9e6, 181.0e6), "c3": (8, 1, 1558.2e6, 846.4e6, 711.8e6)},
 }
 # host-link bandwidths measured earlier on the GB300 machines with pinned
 # buffers (cudaMemcpyAsync, 4 GiB): host-to-device 211, device-to-host 193,
@@ -686,6 +686,8 @@ def bench_config(args, cfg, name, world, rank, local, torch, inputs, so2dr, link
                      "traffic": traffic,
                      # above 1 by the redundant trapezoid planes a launch also computes
                      "traffic_vs_alg": traffic / alg_bytes_per_launch if traffic and alg_bytes_per_launch else None,
+                     "traffic_read_vs_alg": cap[3] / (alg_bytes_per_launch / 2) if traffic and alg_bytes_per_launch else None,
+                     "traffic_write_vs_alg": cap[4] / (alg_bytes_per_launch / 2) if traffic and alg_bytes_per_launch else None,
                      "kernel": ("box2d_fast_kernel" if kind == "box" else "star3d_tb_kernel")
                                + " (k_on-step TB launch)", "peak_kind": ("derived from unit counts and the maximum SM clock" if alu_bound
                                    else peak_kind + " (burst)"),
