@@ -46,3 +46,27 @@ def test_zero_copy_matches_in_core(dims, r, T, dmin, kon, koff, budget, dtype):
     plan.run(oc, in_core=False)
     assert torch.equal(zc.view(torch.uint8), oc.view(torch.uint8))
     plan.close()
+
+
+@pytest.mark.parametrize("split", ["grid", "rounds"])
+@pytest.mark.parametrize("dims,r,kon,koff,dtype", [
+    ((72, 70, 132), 1, 4, 8, so2dr.F32),
+    ((57, 46, 136), 1, 3, 6, so2dr.BF16),
+    ((64, 70, 140), 4, 1, 3, so2dr.F32),
+])
+def test_zero_copy_work_splits(dims, r, kon, koff, dtype, split, monkeypatch):
+    """Zero-copy launches under either work split: in the round split a CTA's
+    pieces mix planes staged from the host and planes from the circular
+    buffer, and the pieces come from the launch's counter."""
+    import torch
+    monkeypatch.setenv("SO2DR_WORK_SPLIT", split)
+    c = [0.4] + [0.1] * 6 if r == 1 else _coeffs(3, r, "star")
+    st = inputs.to_storage(inputs.draw_box(2, dims), dtype)
+    plan = so2dr.Plan(dims, r, "star", c, 2 * koff + kon, min_chunks=4, k_on=kon, k_off=koff, budget_bytes=0,
+                      dtype=dtype)
+    zc = gu.pinned_from_storage(st.copy(), dtype)
+    ic = gu.pinned_from_storage(st.copy(), dtype)
+    plan.run(zc, in_core=3)
+    plan.run(ic, in_core=True)
+    plan.close()
+    assert torch.equal(zc.view(torch.uint8), ic.view(torch.uint8)), "zero-copy != in-core"
