@@ -57,7 +57,7 @@ KERNEL_SRC = {"star": os.path.join(ROOT, "paper_2309_08864_gb300", "csrc", "star
 # the plan's k_on-deep launches (edge chunks clip their trapezoids).
 DRAM_TRAFFIC = {
     # config: (k_off, k_on of the captured plan, bytes per launch, of which read, written)
-    "0f2c9ddf46dd3e47": {"c2": (22, 4, 441.9e6, 260.9e6, 181.0e6), "c3": (8, 1, 1558.2e6, 846.4e6, 711.8e6)},
+    "38a01a2b0291d24d": {"c2": (22, 4, 441.9e6, 260.9e6, 180.9e6), "c3": (8, 1, 1556.0e6, 846.5e6, 709.5e6)},
 }
 # host-link bandwidths measured earlier on the GB300 machines with pinned
 # buffers (cudaMemcpyAsync, 4 GiB): host-to-device 211, device-to-host 193,

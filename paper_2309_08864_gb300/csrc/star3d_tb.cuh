@@ -69,7 +69,9 @@ template <int R, int K> struct StarShape {
     static constexpr int TX = LX - 2 * HXA;             // output columns per tile
     static constexpr int TY = LYT - 2 * HY;             // output rows per tile
     static constexpr int ROWS = LYT + 2 * R;            // staged input rows / level-plane rows
-    static constexpr int NI = 4;                        // input plane slots
+    // input plane slots: radius 4 at one level loads 6 (two CTAs per SM
+    // still fit) and gains 4%; the other shapes lose occupancy or nothing
+    static constexpr int NI = (R == 4 && K == 1) ? 6 : 4;
     static constexpr int PD = NI - 1;                   // planes loaded ahead
     static constexpr int NB = 2;                        // plane slots per intermediate level
     static constexpr int MINB = K == 1 ? 2 : 1;         // CTAs per SM the registers are sized for
