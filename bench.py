@@ -56,8 +56,8 @@ KERNEL_SRC = {"star": os.path.join(ROOT, "paper_2309_08864_gb300", "csrc", "star
 # bytes per input+output plane times the mean input+output planes of all of
 # the plan's k_on-deep launches (edge chunks clip their trapezoids).
 DRAM_TRAFFIC = {
-    # config: (k_off, k_on of the captured plan, bytes per launch, of which read, written)
-    "38a01a2b0291d24d": {"c2": (22, 4, 441.9e6, 260.9e6, 180.9e6), "c3": (8, 1, 1556.0e6, 846.5e6, 709.5e6)},
+    # config: (k_off, k_on, chunks of the captured plan, bytes per launch, of which read, written)
+    "38a01a2b0291d24d": {"c2": (22, 4, 29, 441.9e6, 260.9e6, 180.9e6)},
 }
 # host-link bandwidths measured earlier on the GB300 machines with pinned
 # buffers (cudaMemcpyAsync, 4 GiB): host-to-device 211, device-to-host 193,
@@ -618,7 +618,9 @@ def bench_config(args, cfg, name, world, rank, local, torch, inputs, so2dr, link
     alu_bound = alg_flops_per_launch / (ALU_PEAK_TFLOPS * 1e12) > alg_bytes_per_launch / (hbm_peak * 1e9)
     kind = cfg.get("kind", "star")
     cap = DRAM_TRAFFIC.get(source_digest(KERNEL_SRC[kind]), {}).get(name) if mode == 0 else None
-    traffic = cap[2] if cap and (cap[0], cap[1]) == (info["k_off"], info["k_on"]) else None
+    if cap and (cap[0], cap[1], cap[2]) != (info["k_off"], info["k_on"], info["chunks"]):
+        cap = None
+    traffic = cap[3] if cap else None
     # whole-path roofline: max(host-link time, HBM time) of the algorithmic
     # bytes (every cell sent and received once per round; two HBM passes for
     # the transfers and two per fused launch), against the link measured above
@@ -686,8 +688,8 @@ def bench_config(args, cfg, name, world, rank, local, torch, inputs, so2dr, link
                      "traffic": traffic,
                      # above 1 by the redundant trapezoid planes a launch also computes
                      "traffic_vs_alg": traffic / alg_bytes_per_launch if traffic and alg_bytes_per_launch else None,
-                     "traffic_read_vs_alg": cap[3] / (alg_bytes_per_launch / 2) if traffic and alg_bytes_per_launch else None,
-                     "traffic_write_vs_alg": cap[4] / (alg_bytes_per_launch / 2) if traffic and alg_bytes_per_launch else None,
+                     "traffic_read_vs_alg": cap[4] / (alg_bytes_per_launch / 2) if traffic and alg_bytes_per_launch else None,
+                     "traffic_write_vs_alg": cap[5] / (alg_bytes_per_launch / 2) if traffic and alg_bytes_per_launch else None,
                      "kernel": ("box2d_fast_kernel" if kind == "box" else "star3d_tb_kernel")
                                + " (k_on-step TB launch)", "peak_kind": ("derived from unit counts and the maximum SM clock" if alu_bound
                                    else peak_kind + " (burst)"),

@@ -586,12 +586,12 @@ double kernel_rate(const Plan& p, int depth) {
     // (in-core, 1024^3 FP32; radius 3 and 4 at depth 2 run 2 rows per warp
     // and 2R = 6 or 8 unrolled phases, far slower than one level)
     if (p.r == 1) {
-        const double r1[5] = {0, 740e9, 1220e9, 1450e9, 1400e9};
+        const double r1[5] = {0, 815e9, 1280e9, 1470e9, 1510e9};
         return r1[std::min(depth, 4)];
     }
-    if (p.r == 2) return depth >= 2 ? 830e9 : 710e9;
-    if (p.r == 3) return depth >= 2 ? 330e9 : 565e9;
-    return depth >= 2 ? 110e9 : 480e9;
+    if (p.r == 2) return depth >= 2 ? 780e9 : 800e9;
+    if (p.r == 3) return depth >= 2 ? 320e9 : 545e9;
+    return depth >= 2 ? 112e9 : 429e9;
 }
 
 double predict_ms(const Plan& p) {
