@@ -57,7 +57,7 @@ KERNEL_SRC = {"star": os.path.join(ROOT, "paper_2309_08864_gb300", "csrc", "star
 # the plan's k_on-deep launches (edge chunks clip their trapezoids).
 DRAM_TRAFFIC = {
     # config: (k_off, k_on, chunks of the captured plan, bytes per launch, of which read, written)
-    "38a01a2b0291d24d": {"c2": (22, 4, 29, 441.9e6, 260.9e6, 180.9e6)},
+    "38a01a2b0291d24d": {"c2": (22, 4, 29, 441.9e6, 260.9e6, 180.9e6), "c3": (8, 1, 23, 1815.3e6, 977.8e6, 837.6e6)},
 }
 # host-link bandwidths measured earlier on the GB300 machines with pinned
 # buffers (cudaMemcpyAsync, 4 GiB): host-to-device 211, device-to-host 193,
